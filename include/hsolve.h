@@ -1,0 +1,201 @@
+/*
+ * hsolve.h -- C-ABI of the GB300 hierarchical sparse solver.
+ *
+ * The library computes the approximate factorization of Sec. 2 of
+ * "A distributed-memory hierarchical solver for general sparse linear systems"
+ * (Chen, Pouransari, Rajamanickam, Boman, Darve): clusters of unknowns are
+ * processed level by level; at each cluster the fill-in block is compressed
+ * (Eq. lra), the sparsification operator (Eq. scaling) splits the cluster into
+ * fine and coarse unknowns, the elimination operator (Eq. elim) removes the
+ * fine ones, and the coarse unknowns of sibling clusters form the next level
+ * (Alg. 1).  The factorization is applied by the forward/backward substitution
+ * of Alg. 2 and used as a preconditioner for CG or GMRES (Sec. 5).
+ *
+ * Everything runs on one CUDA device.  All entry points return an
+ * hsolve_status; none aborts, traps or prints.  A handle is used by one host
+ * thread at a time; distinct handles are independent.  Device work is
+ * enqueued on the stream given to hsolve_analyze (NULL = legacy default
+ * stream); calls return after that work has completed unless stated
+ * otherwise.
+ *
+ * Matrix input: CSR with int64 row pointers, int32 column indices and float64
+ * values, host memory, square n x n.  Vector blocks: column-major n x nrhs
+ * with leading dimension ld >= n, float64.
+ */
+#ifndef HSOLVE_H
+#define HSOLVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HSOLVE_OK = 0,
+  HSOLVE_ERR_ARG = -1,            /* invalid argument (sizes, pointers, CSR) */
+  HSOLVE_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+  HSOLVE_ERR_OOM = -3,            /* device allocation failed */
+  HSOLVE_ERR_SINGULAR = -4,       /* zero pivot in an LU factor */
+  HSOLVE_ERR_NOT_SPD = -5,        /* Cholesky met a non-positive pivot */
+  HSOLVE_ERR_NO_CONVERGENCE = -6, /* Krylov solve hit maxit */
+  HSOLVE_ERR_BUDGET = -7,         /* request above a memory budget */
+  HSOLVE_ERR_TIMEOUT = -8,        /* a bounded device wait gave up */
+  HSOLVE_ERR_STATE = -9           /* call out of order (e.g. apply before factor) */
+} hsolve_status;
+
+typedef enum {
+  HSOLVE_FP64 = 0,        /* every factor block and product in float64 */
+  HSOLVE_MIXED_FP32 = 1,  /* float32 blocks, float32 SIMT products,
+                             float64 rank decision, float64 outer Krylov */
+  HSOLVE_MIXED_TF32 = 2,  /* as MIXED_FP32, Schur-complement products on
+                             tcgen05 tensor cores (TF32 in, FP32 accumulate) */
+  HSOLVE_MIXED_BF16 = 3   /* as MIXED_TF32 with BF16 operands */
+} hsolve_precision;
+
+typedef enum { HSOLVE_PCG = 0, HSOLVE_GMRES = 1 } hsolve_krylov;
+
+typedef struct {
+  int64_t n;              /* rows = columns */
+  int64_t nnz;
+  const int64_t* rowptr;  /* [n+1], rowptr[0] = 0, non-decreasing */
+  const int32_t* col;     /* [nnz], each in [0, n) */
+  const double* val;      /* [nnz] */
+} hsolve_csr;
+
+typedef struct {
+  int32_t leaf_size;      /* cluster size at level 0 (bisection stops at or
+                             below it); default 128 */
+  int32_t symmetric;      /* -1 = detect (exact value symmetry), 0 = general
+                             (LU, two-sided compression), 1 = SPD (Cholesky) */
+  int64_t top_size;       /* factor a level densely once it holds at most
+                             this many unknowns (0 = only when one cluster is
+                             left); default 0 */
+  int32_t max_rank;       /* > 0: cap every compression rank at this value
+                             (the fixed-rank option of Sec. 5.1); 0 = none */
+  int32_t gmres_restart;  /* GMRES restart length; default 50 */
+} hsolve_opts;
+
+typedef struct {
+  int32_t iterations;     /* Krylov iterations of the slowest right-hand side */
+  double rel_residual;    /* max over right-hand sides of ||b - A x|| / ||b|| */
+  double factor_ms;       /* device time of the last hsolve_factor */
+  double solve_ms;        /* device time of this solve */
+} hsolve_solve_info;
+
+typedef struct {
+  int32_t levels;         /* levels factored (the dense top counts as one) */
+  int32_t clusters0;      /* clusters at level 0 */
+  int32_t colours_total;  /* sum over levels of colour classes */
+  int32_t top_size;       /* unknowns in the dense top factor (0: none) */
+  int64_t coarse_total;   /* sum over levels of coarse unknowns kept */
+  int64_t factor_bytes;   /* device bytes held by the factorization */
+  int64_t block_bytes;    /* device bytes of the largest level's blocks */
+  int64_t apply_bytes;    /* algorithmic bytes one apply reads and writes
+                             (operators once, vectors as touched), nrhs = 1 */
+  double factor_flops;    /* algorithmic flops of the last factorization */
+  double schur_flops;     /* of which Schur-complement products */
+  int32_t kernel_launches;/* kernels launched by the last hsolve_factor */
+  int32_t precision;      /* hsolve_precision of the last factor */
+} hsolve_stats;
+
+typedef struct hsolve_handle hsolve_handle;
+
+/* Default options. */
+void hsolve_default_opts(hsolve_opts* opts);
+
+/* Analysis (Alg. 1, partition step; Eq. quotient; Sec. 3.2 independence
+ * rule).  Validates the CSR, builds the bisection clusters from coords
+ * (n x dim, row-major, host; NULL = bisection of the index order), the block
+ * pattern of every level and the distance-2 colouring, and uploads the matrix
+ * into device blocks.  The caller keeps ownership of A and coords; the library
+ * copies what it needs.  cuda_stream is a cudaStream_t (NULL = default
+ * stream).  On success *out is a new handle the caller releases with
+ * hsolve_destroy.  Errors: HSOLVE_ERR_ARG for malformed input (out of range
+ * column, non-monotone rowptr, dim not in 1..3), HSOLVE_ERR_OOM,
+ * HSOLVE_ERR_CUDA. */
+hsolve_status hsolve_analyze(const hsolve_csr* A, const double* coords, int dim,
+                             const hsolve_opts* opts, void* cuda_stream,
+                             hsolve_handle** out);
+
+/* Factorization (Alg. 1 with LowRank_Elimination: Eqs. lra, scaling, elim,
+ * perm).  eps is the relative compression tolerance of Eq. lra (|r_jj| <=
+ * eps |r_11| stops the pivoted QR; 0 keeps every nonzero direction, i.e. a
+ * direct solver).  May be called again on the same analysis with another eps
+ * or precision; the previous factorization is released first.  Errors:
+ * HSOLVE_ERR_NOT_SPD / HSOLVE_ERR_SINGULAR (cluster pivot failure; the handle
+ * then holds no factorization), HSOLVE_ERR_OOM, HSOLVE_ERR_CUDA. */
+hsolve_status hsolve_factor(hsolve_handle* h, double eps, hsolve_precision prec);
+
+/* Preconditioner application (Alg. 2): out = M^{-1} rhs where M is the
+ * factorization.  rhs and out are DEVICE pointers, column-major n x nrhs with
+ * leading dimension ld; they may alias.  Errors: HSOLVE_ERR_STATE before a
+ * successful hsolve_factor, HSOLVE_ERR_ARG for nrhs < 1 or ld < n. */
+hsolve_status hsolve_apply(hsolve_handle* h, const double* rhs, double* out,
+                           int nrhs, int64_t ld);
+
+/* Krylov solve of A x = b with the factorization as preconditioner (Sec. 5:
+ * CG for SPD matrices, right-preconditioned flexible GMRES otherwise), in
+ * float64, starting from x = 0, until ||b - A x|| <= tol ||b|| for every
+ * right-hand side or maxit iterations.  b and x are DEVICE pointers
+ * (column-major n x nrhs, leading dimension ld).  info may be NULL.
+ * Errors: HSOLVE_ERR_STATE, HSOLVE_ERR_ARG, HSOLVE_ERR_NO_CONVERGENCE (x
+ * then holds the last iterate). */
+hsolve_status hsolve_solve(hsolve_handle* h, hsolve_krylov krylov, double tol,
+                           int maxit, const double* b, double* x, int nrhs,
+                           int64_t ld, hsolve_solve_info* info);
+
+/* Same as hsolve_solve with b and x in HOST memory: the copies to and from
+ * the device are part of the call. */
+hsolve_status hsolve_solve_host(hsolve_handle* h, hsolve_krylov krylov,
+                                double tol, int maxit, const double* b,
+                                double* x, int nrhs, int64_t ld,
+                                hsolve_solve_info* info);
+
+/* Sparse matrix-vector product y = A x with the analysed matrix, float64,
+ * device pointers (column-major n x nrhs, leading dimension ld). */
+hsolve_status hsolve_spmv(hsolve_handle* h, const double* x, double* y,
+                          int nrhs, int64_t ld);
+
+/* Statistics of the analysis and the last factorization. */
+hsolve_status hsolve_get_stats(const hsolve_handle* h, hsolve_stats* out);
+
+/* Per-level detail, for tests and reports.  Copies up to cap entries of the
+ * ranks (coarse unknowns kept) of level `level`'s clusters into ranks (host),
+ * and writes the number of clusters of that level to *nclu.  Levels are
+ * numbered from 0 (leaves); the dense top level reports zeros. */
+hsolve_status hsolve_get_level(const hsolve_handle* h, int level, int32_t* nclu,
+                               int32_t* sizes, int32_t* ranks, int32_t* colour,
+                               int32_t cap);
+
+/* Level-0 cluster of every unknown: perm[p] = global index of the unknown at
+ * position p of the cluster-ordered vector (host array of n entries). */
+hsolve_status hsolve_get_perm(const hsolve_handle* h, int64_t* perm);
+
+/* Kernel timing of the last factor/apply/solve: per phase name, total device
+ * milliseconds and launch count.  Writes up to cap entries; *count = number
+ * of phases. */
+typedef struct {
+  char name[24];
+  double ms;
+  int32_t launches;
+} hsolve_phase_time;
+hsolve_status hsolve_get_phase_times(const hsolve_handle* h,
+                                     hsolve_phase_time* out, int32_t cap,
+                                     int32_t* count);
+
+/* Enable (1) or disable (0) per-phase CUDA-event timing (off by default; it
+ * adds a synchronisation per phase). */
+hsolve_status hsolve_set_profiling(hsolve_handle* h, int on);
+
+/* Text of the last error on this handle (never NULL). */
+const char* hsolve_last_error(const hsolve_handle* h);
+
+/* Release the handle and all device memory it owns.  NULL is a no-op. */
+void hsolve_destroy(hsolve_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSOLVE_H */

@@ -1,0 +1,259 @@
+"""Pins for the CPU oracle (no GPU).
+
+Each test ties the oracle to something other than itself: a dense direct
+solve (library LU), closed-form Laplacian spectra, LAPACK's pivoted QR, the
+structural fill-in property of Sec. 2.3, a literal N x N restatement of Eqs.
+scaling/elim/perm, or an invariant of the method.  The paper prints no worked
+numerical example, so no value here comes from its text.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from paper_1712_07297_gb300 import inputs as I
+from oracle import hsolver as H
+from oracle import krylov as K
+from oracle import matrix_form as MF
+
+
+def _fac(p, leaf, eps, **kw):
+    return H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=p.symmetric, **kw)
+
+
+def _minv(p, leaf, eps, **kw):
+    return H.solve(_fac(p, leaf, eps, **kw), np.eye(p.n))
+
+
+SMALL = [
+    (lambda: I.poisson((12, 12)), 9),
+    (lambda: I.poisson((6, 6, 6)), 14),
+    (lambda: I.vc_diffusion((6, 6, 6), seed=4), 14),
+    (lambda: I.convection_diffusion((6, 6, 6), 10.0), 14),
+    (lambda: I.convection_diffusion((12, 12), 10.0), 9),
+    (lambda: I.high_contrast((8, 8, 8), seed=2), 16),
+]
+
+
+@pytest.mark.parametrize("mk,leaf", SMALL)
+def test_eps0_is_a_direct_solver(mk, leaf):
+    # Sec. 2.2 / Alg. 1: without truncation the factorization is exact.
+    p = mk()
+    b = I.rhs(p.n, 3, seed=11).T
+    x = H.solve(_fac(p, leaf, 0.0), b)
+    xr = np.linalg.solve(p.dense(), b)
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) < 1e-10
+
+
+def test_eps0_eigenvector_closed_form():
+    shape = (10, 12)
+    p = I.poisson(shape)
+    idx = (3, 5)
+    v = np.ones(p.n)
+    lam = 0.0
+    for d, s in enumerate(shape):
+        v *= np.sin(idx[d] * np.pi * (p.coords[:, d] + 1) / (s + 1))
+        lam += 4 * np.sin(idx[d] * np.pi / (2 * (s + 1))) ** 2
+    x = H.solve(_fac(p, 8, 0.0), v)
+    np.testing.assert_allclose(x, v / lam, atol=1e-12 * np.abs(v / lam).max())
+
+
+@pytest.mark.parametrize("eps", [1e-1, 1e-2])
+def test_1d_laplacian_exact_for_any_eps(eps):
+    # In 1-D every cluster's neighbours are eliminated before fill can reach
+    # it in (colour, index) order, so nothing is dropped: M^{-1} = A^{-1}
+    # and the spectrum of M^{-1} is 1 / (4 sin^2(j pi / (2 (n+1)))).
+    n = 40
+    p = I.poisson((n,))
+    fac = _fac(p, 4, eps)
+    Minv = H.solve(fac, np.eye(n))
+    np.testing.assert_allclose(Minv @ p.dense(), np.eye(n), atol=1e-12)
+    lam = 4 * np.sin(np.arange(1, n + 1) * np.pi / (2 * (n + 1))) ** 2
+    np.testing.assert_allclose(np.sort(np.linalg.eigvalsh((Minv + Minv.T) / 2)), np.sort(1 / lam), rtol=1e-10)
+
+
+@pytest.mark.parametrize("mk,leaf", SMALL[:4])
+def test_error_falls_with_eps(mk, leaf):
+    # Sec. 5.3: a smaller truncation error gives a better preconditioner.
+    p = mk()
+    A = p.dense()
+    errs = []
+    for eps in [3e-1, 1e-2, 1e-4, 1e-7, 0.0]:
+        errs.append(np.linalg.norm(np.eye(p.n) - _minv(p, leaf, eps) @ A, 2))
+    assert all(errs[i + 1] <= errs[i] * 1.05 for i in range(len(errs) - 1)), errs
+    assert errs[-1] < 1e-10 and errs[0] > 1e3 * errs[-2]
+
+
+def test_pcg_iterations_fall_with_eps():
+    p = I.poisson((8, 8, 8))
+    A = p.scipy()
+    b = I.rhs(p.n, 1, seed=3)[0]
+    its = []
+    for eps in [3e-1, 1e-2, 1e-4, 0.0]:
+        fac = _fac(p, 16, eps)
+        _, it, res = K.pcg(A, b, lambda r: H.solve(fac, r), tol=1e-10)
+        assert res <= 1e-10
+        its.append(it)
+    assert its == sorted(its, reverse=True) and its[-1] <= 2 and its[0] > its[-1]
+
+
+def test_spd_preconditioner_is_symmetric():
+    p = I.poisson((6, 6, 6))
+    M = _minv(p, 14, 1e-2)
+    np.testing.assert_allclose(M, M.T, atol=1e-13 * np.abs(M).max())
+    assert np.linalg.eigvalsh((M + M.T) / 2).min() > 0
+
+
+def test_householder_convention():
+    rng = np.random.default_rng(1)
+    for x in [rng.standard_normal(7), -np.abs(rng.standard_normal(5)), np.array([0.0, 3.0, 4.0]),
+              np.array([-2.0, 0.0, 0.0])]:
+        v, tau, beta = H.householder(x)
+        Hm = np.eye(len(x)) - tau * np.outer(v, v)
+        e = np.zeros(len(x))
+        e[0] = beta
+        np.testing.assert_allclose(Hm @ x, e, atol=1e-14 * np.linalg.norm(x))
+        np.testing.assert_allclose(Hm @ Hm.T, np.eye(len(x)), atol=1e-14)
+        assert abs(beta) == pytest.approx(np.linalg.norm(x))
+        assert (beta < 0) == (x[0] >= 0)
+
+
+def test_cpqr_matches_lapack_pivoting():
+    rng = np.random.default_rng(5)
+    G = rng.standard_normal((30, 50)) * np.logspace(0, -3, 50)[rng.permutation(50)]
+    cp = H.cpqr(G, 1e-2)
+    Q, R, P = sla.qr(G, pivoting=True)
+    k = cp["k"]
+    assert list(P[:k]) == cp["piv"]
+    np.testing.assert_allclose(cp["rdiag"], np.abs(np.diag(R))[:k], rtol=1e-12)
+    # truncation rule |r_kk| <= eps |r_11| at the first excluded step
+    d = np.abs(np.diag(R))
+    assert d[k - 1] > 1e-2 * d[0] >= d[k]
+    U = cp["U"]
+    np.testing.assert_allclose(U.T @ U, np.eye(k), atol=1e-13)
+    np.testing.assert_allclose(U @ U.T, Q[:, :k] @ Q[:, :k].T, atol=1e-12)
+
+
+def test_cpqr_rank_follows_singular_value_gap():
+    rng = np.random.default_rng(9)
+    X, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    Y, _ = np.linalg.qr(rng.standard_normal((90, 40)))
+    s = np.array([1.0, 0.7, 0.4, 0.2] + [1e-9] * 36)
+    G = X @ np.diag(s) @ Y.T
+    cp = H.cpqr(G, 1e-4)
+    assert cp["k"] == 4
+    # U spans the dominant left singular subspace
+    np.testing.assert_allclose(cp["U"] @ cp["U"].T, X[:, :4] @ X[:, :4].T, atol=1e-7)
+    assert H.cpqr(G, 0.0)["k"] == 40
+    assert H.cpqr(G, 1e-4, max_rank=2)["k"] == 2
+
+
+def test_cpqr_ties_go_to_lowest_index():
+    G = np.zeros((4, 4))
+    G[1, 0] = 2.0
+    G[0, 1] = -2.0
+    G[2, 2] = 2.0
+    G[3, 3] = 1.0
+    cp = H.cpqr(G, 0.1)
+    assert cp["piv"][:3] == [0, 1, 2]
+    assert cp["k"] == 4
+
+
+def test_complement_is_orthogonal():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((20, 6))
+    V = H.complement(X)
+    assert V.shape == (20, 14)
+    np.testing.assert_allclose(V.T @ X, 0, atol=1e-13)
+    np.testing.assert_allclose(V.T @ V, np.eye(14), atol=1e-13)
+
+
+@pytest.mark.parametrize("mk,leaf,eps", [
+    (lambda: I.poisson((12, 12)), 9, 1e-2),
+    (lambda: I.poisson((6, 6, 6)), 14, 1e-2),
+    (lambda: I.vc_diffusion((6, 6, 6), seed=4), 14, 1e-3),
+    (lambda: I.convection_diffusion((12, 12), 10.0), 9, 1e-2),
+])
+def test_block_oracle_equals_matrix_form(mk, leaf, eps):
+    # Eqs. scaling/elim/perm applied as N x N operators with the Eq. lra
+    # replacement made explicit give the same preconditioner; after each
+    # W_s the fine block is I (Eq. elim), the fine DOFs are decoupled from the
+    # coarse and far ones, and no nonzero block lies beyond distance two
+    # (Sec. 2.3: level-2 fill-in is never created).
+    p = mk()
+    r = MF.factor_dense(p.dense(), p.coords, leaf, eps, symmetric=p.symmetric)
+    Mb = _minv(p, leaf, eps)
+    assert np.abs(Mb - r["Minv"]).max() <= 1e-12 * np.abs(Mb).max()
+    c = r["checks"]
+    assert c["outside_d2"] == 0.0
+    assert c["fine_identity"] < 1e-10 and c["fine_decoupled"] < 1e-10 and c.get("fine_far", 0) < 1e-12
+    assert c["final_identity"] < 1e-10
+
+
+def test_colouring_is_distance_two():
+    p = I.poisson((16, 16, 16))
+    fac = _fac(p, 32, 1e-2)
+    for lv in fac.levels[:-1]:
+        for i in range(lv.nclu):
+            for j in lv.adj[i] | lv.d2[i]:
+                assert lv.colour[i] != lv.colour[j]
+        assert lv.order == sorted(range(lv.nclu), key=lambda i: (lv.colour[i], i))
+
+
+def test_rcb_boxes():
+    p = I.poisson((8, 8))
+    depth, leaves = H.rcb_leaves(p.coords, 8)
+    assert depth == 3 and len(leaves) == 8
+    for lf in leaves:
+        c = p.coords[lf]
+        ext = tuple(c.max(0) - c.min(0) + 1)
+        assert ext == (2, 4)       # x, y, x splits: 8x8 -> 4x8 -> 4x4 -> 2x4
+    p3 = I.poisson((16, 16, 16))
+    _, lv3 = H.rcb_leaves(p3.coords, 128)
+    assert len(lv3) == 32
+    assert {tuple(p3.coords[l].max(0) - p3.coords[l].min(0) + 1) for l in lv3} == {(4, 4, 8)}
+    assert np.array_equal(np.sort(np.concatenate(lv3)), np.arange(p3.n))
+
+
+def test_no_fill_cluster_is_block_cholesky():
+    # Sec. 2.2: with no fill-in, E_s = I and W_s is one block-Cholesky step.
+    p = I.poisson((12, 12))
+    fac = _fac(p, 9, 1e-2)
+    lv = fac.levels[0]
+    A = p.dense()[np.ix_(fac.perm, fac.perm)]
+    s = lv.order[0]
+    cf = lv.factors[s]
+    assert cf.k == 0 and cf.TL is None
+    o = lv.offsets
+    S = slice(o[s], o[s + 1])
+    N = np.concatenate([np.arange(o[n], o[n + 1]) for n, _ in cf.nbrs])
+    Ass, AsN = A[S, S], A[S][:, N]
+    np.testing.assert_allclose(cf.LF @ cf.LF.T, Ass, atol=1e-13)
+    np.testing.assert_allclose(cf.BR.T @ cf.BR, AsN.T @ np.linalg.solve(Ass, AsN), atol=1e-13)
+
+
+def test_fixed_rank_caps_ranks():
+    p = I.poisson((16, 16))
+    fac = _fac(p, 16, 1e-6, max_rank=3)
+    assert max(f.k for f in fac.levels[0].factors.values()) <= 3
+
+
+def test_dense_top_switch():
+    p = I.poisson((12, 12))
+    b = I.rhs(p.n, 1, seed=1)[0]
+    x0 = H.solve(_fac(p, 9, 0.0, top_size=10 ** 9), b)   # one dense factor
+    assert len(_fac(p, 9, 0.0, top_size=10 ** 9).levels) == 1
+    np.testing.assert_allclose(p.scipy() @ x0, b, atol=1e-12)
+
+
+@pytest.mark.parametrize("method", ["pcg", "gmres"])
+def test_krylov_against_direct(method):
+    p = I.poisson((10, 10)) if method == "pcg" else I.convection_diffusion((10, 10))
+    A = p.scipy()
+    b = I.rhs(p.n, 1, seed=2)[0]
+    fn = K.pcg if method == "pcg" else (lambda *a, **k: K.fgmres(*a, restart=20, **k))
+    x, it, res = fn(A, b, lambda r: r, tol=1e-10, maxit=2000)
+    np.testing.assert_allclose(x, np.linalg.solve(p.dense(), b), rtol=1e-8, atol=1e-9)
+    assert res <= 1e-10 and it > 5
+    fac = _fac(p, 9, 0.0)
+    x1, it1, res1 = fn(A, b, lambda r: H.solve(fac, r), tol=1e-10)
+    assert it1 <= 2 and res1 <= 1e-10
