@@ -1,0 +1,353 @@
+"""Benchmark: factor + solve latency of the hierarchical solver on one GB300.
+
+One step = hsolve_factor (all levels of Alg. 1) + hsolve_solve (float64 PCG
+preconditioned by Alg. 2) of the 3D 7-point Poisson problem on a 64^3 grid
+(N = 262,144), clusters of 128 unknowns, eps = 1e-2, one right-hand side with
+entries uniform in [-1, 1], to a relative residual of 1e-10.  Analysis and the
+matrix upload are outside the timed region.
+
+The JSON line reports the float64 path (`value`) and the mixed-precision path
+(`mixed`), p50/p99 over the steps, an end-to-end figure through the host-buffer
+entry point, the roofline of the dominant kernel, the CPU oracle baseline and
+the SM clocks seen while timing.
+
+`--impl reference` times the CPU oracle (float64 numpy restatement of the
+method) on the host cores instead.
+
+Multi-GPU: the method runs on one GPU with no sharding; under torchrun every
+rank runs an independent replica and rank 0 reports the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "factor+solve ms to 1e-10 rel. residual, mixed vs FP64 on GPU; p50/p99 latency"
+WORKLOAD = "poisson3d_64"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_tflops(dtype: str, sm_mhz: float) -> float:
+    """Plain-ALU peaks from unit counts and clock: 152 SMs x 128 FP32 lanes x
+    2 flops (FMA); float64 at 1/64 of the float32 rate (2 FP64 FMA per clock
+    per SM, the rate behind the 1.25 TFLOP/s nominal figure)."""
+    fp32 = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    return fp32 if dtype == "f32" else fp32 / 64.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for i, nm in enumerate(names):
+                if "Active" in s[5 + i] and "Not" not in s[5 + i]:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_1712_07297_gb300 import build, hsolve
+    from paper_1712_07297_gb300 import inputs as I
+
+    build.build()
+    dev = rank % max(torch.cuda.device_count(), 1)
+    torch.cuda.set_device(dev)
+    prob, st = I.workload(args.workload)
+    eps = args.eps if args.eps is not None else st["eps"]
+    leaf = st["leaf"]
+    nrhs = args.nrhs or st["nrhs"]
+    stream = torch.cuda.current_stream()
+    s = hsolve.Solver.from_problem(prob, leaf_size=leaf, symmetric=1 if prob.spd else 0,
+                                   stream=stream)
+    krylov = "pcg" if prob.spd else "gmres"
+    b_host = I.rhs(prob.n, nrhs, seed=st["rhs_seed"])
+    b = torch.from_numpy(b_host).cuda()
+    x = torch.empty_like(b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_step(prec):
+        s.factor(eps, prec)
+        _, info = s.solve(b, x, krylov=krylov, tol=1e-10, maxit=500)
+        return info
+
+    def timed_steps(prec, steps, warmup):
+        for _ in range(warmup):
+            one_step(prec)
+        times, infos = [], []
+        for _ in range(steps):
+            flush.zero_()  # L2 flush between timed steps (256 MB > 129 MB L2)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = one_step(prec)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(info)
+        return times, infos
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = s.stats()["launches_total"]
+    with ClockSampler(dev) as clk:
+        t64, i64 = timed_steps("fp64", args.steps, args.warmup)
+    launches1 = s.stats()["launches_total"]
+    torch.cuda.synchronize()
+    st64 = s.stats()
+    tmx, imx = timed_steps(args.mixed, args.steps, max(1, args.warmup // 2))
+    stmx = s.stats()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    # end to end through the host-buffer entry point (copies in the region)
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.factor(eps, "fp64")
+        xh, info = s.solve_host(b_host, krylov=krylov, tol=1e-10, maxit=500)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+
+    # per-kernel durations: one extra profiled step per precision
+    s.set_profiling(True)
+    one_step("fp64")
+    ph64 = s.phase_times()
+    s.set_profiling(False)
+    s.set_profiling(True)
+    one_step(args.mixed)
+    phmx = s.phase_times()
+    s.set_profiling(False)
+    s.factor(eps, "fp64")
+
+    peaks, pk_src = _peaks()
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    dom = max((k for k in ph64 if k not in ("upload", "assemble")), key=lambda k: ph64[k][0])
+    work = {"schur": st64["schur_flops"], "prep": st64["prep_flops"],
+            "gemm_coarse": st64["gemm_flops"], "gemm_fill": st64["gemm_flops"]}
+    ms_dom, nl_dom = ph64[dom]
+    fl = work.get(dom, st64["factor_flops"])
+    ach = fl / (ms_dom * 1e-3) / 1e12
+    peak = alu_peak_tflops("f64", sm_mhz)
+    roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None, "launches": nl_dom,
+            "ms_total": ms_dom, "peak_source": "derived (152 SM x 2 FP64 FMA/clk x SM clock)"}
+
+    res = {
+        "metric": METRIC,
+        "value": statistics.mean(t64),
+        "unit": "ms",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": statistics.mean(t64),
+        "p50_ms": _pct(t64, 50),
+        "p99_ms": _pct(t64, 99),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "3D 7-point Poisson 64^3 (N=262144), clusters of 128, eps=1e-2, "
+                               "1 RHS U[-1,1], PCG to 1e-10",
+                   "n": prob.n, "nnz": prob.nnz, "leaf": leaf, "eps": eps, "nrhs": nrhs,
+                   "krylov": krylov, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iterations": i64[-1].iterations,
+        "rel_residual": max(i.rel_residual for i in i64),
+        "factor_ms": i64[-1].factor_ms,
+        "solve_ms": i64[-1].solve_ms,
+        "mixed": {"precision": args.mixed, "ms_per_step": statistics.mean(tmx),
+                  "p50_ms": _pct(tmx, 50), "p99_ms": _pct(tmx, 99),
+                  "iterations": imx[-1].iterations,
+                  "rel_residual": max(i.rel_residual for i in imx),
+                  "factor_ms": imx[-1].factor_ms, "solve_ms": imx[-1].solve_ms},
+        "e2e": {"value": statistics.mean(e2e), "unit": "ms",
+                "h2d_bytes_per_step": 8 * prob.n * nrhs, "d2h_bytes_per_step": 8 * prob.n * nrhs},
+        "gpu_launches": int((launches1 - launches0) / max(args.steps + args.warmup, 1)),
+        "gpu_launches_note": "library kernels per step (factor + solve), counted by the library",
+        "roofline": roof,
+        "phases_fp64": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in ph64.items()},
+        "phases_mixed": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in phmx.items()},
+        "stats": {"levels": st64["levels"], "colours_total": st64["colours_total"],
+                  "factor_bytes": st64["factor_bytes"], "apply_bytes": st64["apply_bytes"],
+                  "factor_gflop": st64["factor_flops"] / 1e9},
+        "clocks": clocks,
+        "peaks_source": pk_src,
+    }
+    s.close()
+    return res
+
+
+def cpu_baseline(args, steps=1):
+    """The float64 oracle on the host cores, on a bounded sample: the same
+    problem family, leaf, eps and tolerance on a 32^3 grid (N/8), with the
+    time scaled by 8 (the method's O(N) work, Sec. 4) to the 64^3 unit."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = r"""
+import sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+from paper_1712_07297_gb300 import inputs as I
+from oracle import hsolver as H, krylov as K
+p = I.poisson((32, 32, 32))
+b = I.rhs(p.n, 1, seed=1001)[0]
+A = p.scipy()
+ts = []
+for _ in range(%d):
+    t0 = time.perf_counter()
+    fac = H.factor(p.rowptr, p.col, p.val, p.coords, 128, %r, symmetric=True)
+    x, it, res = K.pcg(A, b, lambda r: H.solve(fac, r), tol=1e-10, maxit=500)
+    ts.append(time.perf_counter() - t0)
+print(json.dumps({"s": ts, "it": it, "res": res}))
+""" % (ROOT, steps, args.eps if args.eps is not None else 1e-2)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return None, r.stderr[-400:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d, None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--eps", type=float, default=None)
+    ap.add_argument("--nrhs", type=int, default=0)
+    ap.add_argument("--mixed", default="mixed_fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        d, err = cpu_baseline(args, steps=max(1, args.steps))
+        if d is None:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + err}))
+            return
+        ms = [8 * t * 1e3 for t in d["s"]]
+        v = statistics.mean(ms)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": "ms",
+            "n_gpus": world, "steps": len(ms), "warmup": 0, "ms_per_step": v,
+            "p50_ms": _pct(ms, 50), "p99_ms": _pct(ms, 99), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "3D 7-point Poisson 64^3 (N=262144), clusters of 128, "
+                                   "eps=1e-2, 1 RHS U[-1,1], PCG to 1e-10"},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": "3D Poisson 32^3 (N/8), same leaf/eps/tol, time x 8"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "iterations": d["it"], "rel_residual": d["res"]}))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+        dist.init_process_group("nccl")
+    res = run_gpu(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([res["ms_per_step"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        res["value"] = res["ms_per_step"] = float(t.item())
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            d, err = cpu_baseline(args, steps=1)
+            if d is not None:
+                v = 8 * d["s"][0] * 1e3
+                res["cpu_baseline"] = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                                       "sample": "3D Poisson 32^3 (N/8), same leaf/eps/tol, "
+                                                 "time x 8 (O(N) work, Sec. 4)"}
+            else:
+                res["cpu_baseline"] = {"value": None, "error": err}
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

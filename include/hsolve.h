@@ -94,9 +94,14 @@ typedef struct {
   int64_t apply_bytes;    /* algorithmic bytes one apply reads and writes
                              (operators once, vectors as touched), nrhs = 1 */
   double factor_flops;    /* algorithmic flops of the last factorization */
-  double schur_flops;     /* of which Schur-complement products */
+  double schur_flops;     /* of which Schur-complement products (Eq. elim) */
+  double prep_flops;      /* of which per-cluster dense work (factor of
+                             A_ss, pivoted QR, complement, T, F) */
+  double gemm_flops;      /* of which coarse-row / fine-factor products
+                             T' A_sN and coarse-to-far products C U^T A_sw */
   int32_t kernel_launches;/* kernels launched by the last hsolve_factor */
   int32_t precision;      /* hsolve_precision of the last factor */
+  int64_t launches_total; /* kernels launched by the library in this process */
 } hsolve_stats;
 
 typedef struct hsolve_handle hsolve_handle;

@@ -27,9 +27,11 @@ Readings of points the paper leaves open (each is also listed in the design doc):
     recomputed at every step; the pivot is the column of largest remaining
     norm, near-ties (squared norm within a relative 1e-10 of the largest)
     going to the lowest original column index; the factorization stops at the
-    first step j with |r_jj| <= eps |r_11| (eps > 0) or when the remaining
-    columns are all exactly zero.  k = number of kept steps, U = first k
-    columns of Q.
+    first step j with |r_jj| <= eps |r_11| (eps > 0), with |r_jj| <=
+    1e-14 max|A_ss| (a fill block at the rounding level of the cluster's own
+    diagonal block is zero in exact arithmetic; without this floor its
+    "rank" is decided by rounding noise), or when the remaining columns are
+    all exactly zero.  k = number of kept steps, U = first k columns of Q.
   * k = 0 (no fill): E_s = I and the step is one block-Cholesky/LU step
     (Sec. 2.2).  k = m: the cluster is left untouched (E_s = I, all coarse).
   * Householder convention: v = x - beta e1, beta = -sign(x_0) ||x||
@@ -55,6 +57,10 @@ import numpy as np
 import scipy.linalg as sla
 
 PIVOT_TIE_RTOL = 1e-10
+# A fill direction whose |r_jj| is at most this fraction of max |A_ss| is
+# rounding noise of a block that is zero in exact arithmetic; it is dropped
+# whatever eps is (see the module docstring).
+NOISE_FLOOR = 1e-14
 
 
 # ---------------------------------------------------------------------------
@@ -145,12 +151,14 @@ def householder(x: np.ndarray):
     return v, tau, beta
 
 
-def cpqr(G: np.ndarray, eps: float, max_rank: int | None = None):
+def cpqr(G: np.ndarray, eps: float, max_rank: int | None = None, floor: float = 0.0):
     """Householder QR with column pivoting, truncated at eps (Eq. lra).
 
-    Returns dict(k, U, piv, rdiag, margin) where U (m x k) has orthonormal
-    columns spanning the kept directions, piv are the chosen original column
-    indices and rdiag the |r_jj| of every examined step.
+    The factorization stops at the first step whose |r_jj| is at or below
+    eps |r_11| (eps > 0) or at or below the absolute `floor`.  Returns
+    dict(k, U, piv, rdiag, margin) where U (m x k) has orthonormal columns
+    spanning the kept directions, piv are the chosen original column indices
+    and rdiag the |r_jj| of every kept step.
     """
     m, c = G.shape
     A = np.array(G, dtype=np.float64, copy=True)
@@ -171,6 +179,8 @@ def cpqr(G: np.ndarray, eps: float, max_rank: int | None = None):
         r = np.sqrt(nrm2[p])
         if j == 0:
             r11 = r
+        if r <= floor:
+            break
         if eps > 0.0:
             margin = min(margin, abs(r / (eps * r11) - 1.0))
             if r <= eps * r11:
@@ -317,7 +327,7 @@ def _process_cluster(s, blocks, cur, adj, d2, eps, symmetric, max_rank):
     if G.shape[1] == 0:
         cp = dict(k=0, U=np.zeros((m, 0)), piv=[], rdiag=[], margin=np.inf)
     else:
-        cp = cpqr(G, eps, max_rank)
+        cp = cpqr(G, eps, max_rank, floor=NOISE_FLOOR * np.abs(Ass).max())
     k = cp["k"]
     widths = [(n, cur[n]) for n in N]
     AsN = np.hstack([blocks[(s, n)][:m, :w] for n, w in widths]) if N else np.zeros((m, 0))

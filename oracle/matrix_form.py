@@ -89,13 +89,14 @@ def factor_dense(A: np.ndarray, coords, leaf: int, eps: float, symmetric=True):
             if not symmetric:
                 G = np.hstack([G, Abar[np.ix_(Widx, S)].T])
             G = G[:, np.any(G != 0.0, axis=0)] if G.size else G.reshape(m, 0)
-            k = H.cpqr(G, eps)["k"] if G.shape[1] else 0
+            floor = H.NOISE_FLOOR * np.abs(Ass).max()
+            k = H.cpqr(G, eps, floor=floor)["k"] if G.shape[1] else 0
             if k == m:
                 continue
             EL = np.eye(n)
             ER = np.eye(n)
             if k > 0:
-                U = H.cpqr(G, eps)["U"]
+                U = H.cpqr(G, eps, floor=floor)["U"]
                 # Eq. lra: the fill block is replaced by its low-rank
                 # approximation U Z, Z = U^T A_sw (and A_ws by (A_ws U) U^T)
                 if Widx:

@@ -1,0 +1,181 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hsolve.h"
+
+namespace hs {
+
+// Kernels launched by this process through the library (all handles).
+int64_t launches_total();
+void count_launch(int n = 1);
+
+// ---------------------------------------------------------------------------
+// Device-side error word: the first failing cluster records its code and id.
+// ---------------------------------------------------------------------------
+struct DevError {
+  int code;     // 0 = ok, else an hsolve_status value
+  int cluster;  // cluster id (level-local)
+  int level;
+  int pad;
+};
+
+// ---------------------------------------------------------------------------
+// Host analysis (analyze.cpp): clusters, patterns, colouring.
+// ---------------------------------------------------------------------------
+struct LevelPattern {
+  int nclu = 0;
+  std::vector<int> m;          // unknowns per cluster at level start
+  std::vector<int> ld;         // leading dimension of cluster i's block rows
+  std::vector<int64_t> voff;   // vector slot offsets (prefix sum of m)
+  // Block pattern (CSR over clusters, columns ascending): self, neighbours
+  // (A_B of the level) and distance-2 clusters (where fill-in can live).
+  std::vector<int> ptr, col;
+  std::vector<int8_t> kind;    // 0 self, 1 neighbour, 2 distance two
+  std::vector<int64_t> off;    // block offset in the level arena (elements)
+  int64_t arena_elems = 0;
+  std::vector<int> colour;
+  std::vector<std::vector<int>> classes;  // clusters of each colour, ascending
+  int64_t find(int i, int j) const;       // pattern index of (i, j) or -1
+};
+
+// Recursive coordinate bisection to a uniform depth (Alg. 1 partition step).
+// Returns depth; leaves holds 2^depth sorted index lists in tree order.
+int rcb_leaves(int64_t n, const double* coords, int dim, int leaf,
+               std::vector<std::vector<int64_t>>& leaves);
+
+// Fill in ld, voff, the pattern (from neighbour sets), block offsets and the
+// greedy distance-2 colouring.  adj[i] = sorted neighbours (excluding i).
+void build_level_pattern(LevelPattern& L, const std::vector<std::vector<int>>& adj);
+
+int round_up(int x, int a);
+
+// ---------------------------------------------------------------------------
+// Kernel launch wrappers (kernels.cu).  `real` is float or double.
+// ---------------------------------------------------------------------------
+
+// Per-cluster task of the dense "prep" phase.
+struct PrepTask {
+  int s;            // level-local cluster id
+  int m;            // unknowns
+  int ld;           // ld of cluster s's block rows
+  int ncolG;        // fill columns gathered into G
+  int64_t a_ss;     // offset of block (s,s) in the arena
+  int64_t gcol;     // offset into the column-descriptor arrays
+  int64_t ws;       // workspace offset (elements of real)
+  int64_t wsd;      // workspace offset (doubles) for norms
+  int64_t T;        // factor offset of T' (m x m, ld m)
+  int64_t TR;       // factor offset of T'_R (general only)
+  int64_t D;        // workspace offset of D = C U^T (k x m, ld m)
+  int64_t D2;       // workspace offset of D2 = C^T U^T (general only)
+};
+
+// Grouped GEMM task: C (M x N, ldc) = A (M x K, lda) * Bg, where column j of
+// Bg starts at bptr[j] with element stride bstr[j].  M, N, K may be bounded
+// by the device rank array: see kernels.cu.
+struct GemmTask {
+  int s;
+  int M, N, K;         // upper bounds (rows of A, columns of Bg, inner)
+  int mode;            // how M/K derive from the rank k = rank[s] (see kernels.cu)
+  int lda, ldc;
+  int64_t A, C;        // offsets (A in factor or workspace arena, C in ws/factor)
+  int64_t bcol;        // offset into column descriptor arrays
+};
+
+// Schur update task: C_mapped -= P^T Q with P, Q (f x nw, ld ldy) taken
+// from rows k..m of Y-type factor storage.
+struct SchurTask {
+  int s;
+  int m;            // rows of the Y storage (ld)
+  int nw;           // sum of neighbour widths
+  int nb;           // neighbours
+  int64_t P, Q;     // factor offsets of the P/Q storages
+  int64_t map;      // offset into the packed row/col map array (nw entries)
+  int64_t base;     // offset into the block-base table (nb*nb entries)
+  int64_t ldn;      // offset into the neighbour-ld array (nb entries)
+};
+
+// Scatter of coarse rows/columns into the blocks after a cluster step.
+struct ScatterSeg {
+  int s;            // cluster
+  int width;        // columns of the segment
+  int ld_s, ld_o;   // lds of cluster s and of the other cluster
+  int64_t src;      // offset of the segment's first column in the source (rows 0..k)
+  int64_t src2;     // same for the transposed side (general) or -1 for symmetric
+  int ld_src;       // leading dimension of the source
+  int m;            // unknowns of s (k == m means untouched: nothing to do)
+  int64_t dst_row;  // block (s, o) offset: rows 0..k receive the source
+  int64_t dst_col;  // block (o, s) offset: columns 0..k receive the transpose
+};
+
+struct CopyTask {   // child block -> parent block (next-level assembly)
+  int rows, cols, ld_src, ld_dst;
+  int64_t src, dst;
+};
+
+struct ApplyRec {   // one cluster's factor, as the substitution sweeps use it
+  int m, k, nw, sym;
+  int64_t voff;     // slot offset in the level vector
+  int64_t T, TR;    // T' (and T'_R) offsets in the factor arena
+  int64_t Y, XT;    // B_R storage (rows k..m of Y) and B_L^T storage (XT)
+  int64_t map;      // offset into the vector-index map (nw entries)
+};
+
+template <typename real>
+struct Launch {
+  static void prep(const PrepTask* tasks_dev, int ntask, real* arena, real* fac,
+                   real* ws, double* wsd, const int64_t* gptr, const int* gstr,
+                   int* rank, double eps, int sym, int max_rank, int maxm,
+                   DevError* err, int level, cudaStream_t st);
+  static void gemm_gather(const GemmTask* tasks_dev, int ntask, int maxM, int maxN,
+                          const real* Abase, real* Cbase, const real* Bbase,
+                          const int64_t* bptr, const int* bstr, const int* rank,
+                          cudaStream_t st);
+  static void schur(const SchurTask* tasks_dev, int ntask, int maxnw, const real* fac,
+                    real* arena, const int* map, const int64_t* base, const int* ldn,
+                    const int* rank, cudaStream_t st);
+  static void scatter(const ScatterSeg* segs_dev, int nseg, int maxw, const real* src,
+                      real* arena, const int* rank, cudaStream_t st);
+  static void copy_blocks(const CopyTask* tasks_dev, int ntask, const real* src, real* dst,
+                          cudaStream_t st);
+  static void apply_fwd(const ApplyRec* recs, const int* ids, int nids, const real* fac,
+                        const int64_t* vmap, real* y, int64_t ldy, int nrhs, int maxm,
+                        cudaStream_t st);
+  static void apply_bwd(const ApplyRec* recs, const int* ids, int nids, const real* fac,
+                        const int64_t* vmap, real* y, int64_t ldy, int nrhs, int maxm,
+                        cudaStream_t st);
+  static void scatter_csr(const int64_t* dst, const double* val, int64_t nnz, real* arena,
+                          cudaStream_t st);
+  static void gather_vec(const int64_t* idx, int64_t n, const real* src, int64_t lds,
+                         real* dst, int64_t ldd, int nrhs, cudaStream_t st);
+  static void scatter_vec(const int64_t* idx, int64_t n, const real* src, int64_t lds,
+                          real* dst, int64_t ldd, int nrhs, cudaStream_t st);
+  static void perm_in(const int64_t* perm, int64_t n, const double* src, int64_t lds,
+                      real* dst, int64_t ldd, int nrhs, cudaStream_t st);
+  static void perm_out(const int64_t* perm, int64_t n, const real* src, int64_t lds,
+                       double* dst, int64_t ldd, int nrhs, cudaStream_t st);
+  static void dense_top_factor(real* a, int n, int sym, int* piv, DevError* err,
+                               cudaStream_t st);
+  static void dense_top_solve(const real* a, int n, int sym, const int* piv, real* y,
+                              int64_t ldy, int nrhs, cudaStream_t st);
+};
+
+// float64 Krylov helpers (kernels.cu)
+void spmv_csr(int64_t n, const int64_t* rp, const int* ci, const double* v, const double* x,
+              int64_t ldx, double* y, int64_t ldy, int nrhs, cudaStream_t st);
+void dots(int64_t n, const double* a, int64_t lda, const double* b, int64_t ldb, int nrhs,
+          double* out, cudaStream_t st);
+void multi_dot(int64_t n, int nv, const double* V, int64_t ldv, const double* w, double* out,
+               cudaStream_t st);
+void multi_axpy(int64_t n, int nv, const double* V, int64_t ldv, const double* coef,
+                double sign, double* w, cudaStream_t st);
+void axpby_cols(int64_t n, int nrhs, const double* alpha, const double* x, int64_t ldx,
+                const double* beta, double* y, int64_t ldy, cudaStream_t st);
+
+}  // namespace hs

@@ -1,0 +1,1373 @@
+// C-ABI entry points and the host-side driver of the hierarchical solver.
+//
+// hsolve_analyze  Alg. 1 partition step (recursive coordinate bisection),
+//                 Eq. quotient block pattern, distance-2 colouring (Sec. 3.2).
+// hsolve_factor   Alg. 1: per level, per colour class, one batched launch per
+//                 phase of LowRank_Elimination (Eqs. lra, scaling, elim, perm);
+//                 sibling clusters' coarse unknowns form the next level.
+// hsolve_apply    Alg. 2 forward/backward substitution.
+// hsolve_solve    Sec. 5 usage: preconditioned CG / flexible GMRES in float64.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.h"
+
+using namespace hs;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+
+struct Status {
+  hsolve_status code = HSOLVE_OK;
+  std::string msg;
+};
+
+#define HS_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      throw Fail(e_ == cudaErrorMemoryAllocation ? HSOLVE_ERR_OOM : HSOLVE_ERR_CUDA, \
+                 std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    }                                                                              \
+  } while (0)
+
+struct Fail {
+  hsolve_status code;
+  std::string msg;
+  Fail(hsolve_status c, std::string m) : code(c), msg(std::move(m)) {}
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p;
+      bytes = o.bytes;
+      o.p = nullptr;
+      o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void alloc(size_t b) {
+    release();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      throw Fail(HSOLVE_ERR_OOM, "cudaMalloc of " + std::to_string(b) + " bytes failed");
+    }
+    bytes = b;
+  }
+  void ensure(size_t b) {
+    if (b > bytes) alloc(b);
+  }
+  template <typename T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Host blob of several arrays uploaded with one copy.
+struct Blob {
+  std::vector<char> h;
+  size_t add_raw(const void* src, size_t bytes) {
+    size_t o = (h.size() + 15) & ~size_t(15);
+    h.resize(o + bytes);
+    if (bytes) std::memcpy(h.data() + o, src, bytes);
+    return o;
+  }
+  template <typename T>
+  size_t add(const std::vector<T>& v) { return add_raw(v.data(), v.size() * sizeof(T)); }
+};
+
+struct PinnedBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~PinnedBuf() {
+    if (p) cudaFreeHost(p);
+  }
+  void ensure(size_t b) {
+    if (b <= bytes) return;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    if (cudaMallocHost(&p, b) != cudaSuccess) {
+      cudaGetLastError();
+      throw Fail(HSOLVE_ERR_OOM, "cudaMallocHost failed");
+    }
+    bytes = b;
+  }
+};
+
+struct PhaseTimer {
+  std::string name;
+  double ms = 0;
+  int launches = 0;
+};
+
+// One factored level.
+struct FLevel {
+  LevelPattern P;
+  std::vector<int> k;                 // coarse unknowns kept per cluster
+  std::vector<std::vector<int>> cls;  // processed clusters per colour class
+  DevBuf fac;                         // factor arena (real)
+  DevBuf recs;                        // ApplyRec per cluster
+  DevBuf vmap;                        // int64 vector index maps
+  DevBuf ids;                         // int cluster ids, class by class
+  std::vector<int> cls_off;           // offsets of each class in ids
+  std::vector<int> cls_maxm;          // apply smem bound per class
+  DevBuf next_idx;                    // int64 gather map to the next level
+  int64_t next_n = 0;
+  DevBuf vec;                         // level vector buffer (real)
+  size_t vec_bytes = 0;
+  bool top = false;
+};
+
+}  // namespace
+
+struct hsolve_handle {
+  int64_t n = 0, nnz = 0;
+  std::vector<int64_t> rowptr;
+  std::vector<int> col;
+  std::vector<double> val;
+  DevBuf d_rowptr, d_col, d_val;
+  int symmetric = 1;
+  hsolve_opts opts{};
+  cudaStream_t st = nullptr;
+  std::vector<int64_t> perm;
+  DevBuf d_perm;
+  LevelPattern L0;
+  std::vector<std::vector<int>> adj0;
+  std::vector<int64_t> csr_dst;  // arena destination of every nonzero at level 0
+  DevBuf d_csr_dst;
+  // factorization
+  std::vector<std::unique_ptr<FLevel>> F;
+  int prec = -1;
+  bool factored = false;
+  double factor_ms = 0;
+  double factor_flops = 0, schur_flops = 0, prep_flops = 0, gemm_flops = 0;
+  int64_t apply_bytes = 0, factor_bytes = 0, block_bytes = 0;
+  int launches = 0;
+  int colours_total = 0;
+  int64_t coarse_total = 0;
+  // scratch
+  DevBuf d_err;
+  DevBuf ws, wsd, blob_dev;
+  PinnedBuf pin;
+  DevBuf kry;  // Krylov vectors
+  DevBuf dots;
+  PinnedBuf pin_small;
+  bool profiling = false;
+  std::vector<PhaseTimer> phases;
+  std::string err;
+};
+
+namespace {
+
+hsolve_status set_err(hsolve_handle* h, hsolve_status c, const std::string& m) {
+  if (h) h->err = m;
+  return c;
+}
+
+void phase_add(hsolve_handle* h, const char* name, double ms, int launches) {
+  for (auto& p : h->phases)
+    if (p.name == name) {
+      p.ms += ms;
+      p.launches += launches;
+      return;
+    }
+  PhaseTimer t;
+  t.name = name;
+  t.ms = ms;
+  t.launches = launches;
+  h->phases.push_back(t);
+}
+
+// Upload a host blob to the handle's device blob buffer; returns the base.
+char* upload_blob(hsolve_handle* h, const Blob& b) {
+  size_t bytes = std::max<size_t>(b.h.size(), 16);
+  h->pin.ensure(bytes);
+  // the previous upload's kernels have completed: every user syncs first
+  std::memcpy(h->pin.p, b.h.data(), b.h.size());
+  h->blob_dev.ensure(bytes);
+  HS_CUDA(cudaMemcpyAsync(h->blob_dev.p, h->pin.p, b.h.size(), cudaMemcpyHostToDevice, h->st));
+  return h->blob_dev.as<char>();
+}
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  bool on = false;
+  EventPair(bool enable) : on(enable) {
+    if (on) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+    }
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+// Per-phase timing helper: records an event pair around a lambda when
+// profiling is on, otherwise just runs it.
+template <typename Fn>
+void timed(hsolve_handle* h, const char* name, int launches, Fn&& fn) {
+  h->launches += launches;
+  if (!h->profiling) {
+    fn();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+      throw Fail(HSOLVE_ERR_CUDA, std::string(name) + " launch: " + cudaGetErrorString(e));
+    return;
+  }
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, h->st);
+  fn();
+  cudaEventRecord(b, h->st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    throw Fail(HSOLVE_ERR_CUDA, std::string(name) + " launch: " + cudaGetErrorString(e));
+  cudaEventSynchronize(b);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  phase_add(h, name, ms, launches);
+}
+
+void check_dev_error(hsolve_handle* h) {
+  DevError e{};
+  HS_CUDA(cudaMemcpyAsync(&e, h->d_err.p, sizeof(DevError), cudaMemcpyDeviceToHost, h->st));
+  HS_CUDA(cudaStreamSynchronize(h->st));
+  if (e.code != 0) {
+    throw Fail((hsolve_status)e.code, std::string(e.code == HSOLVE_ERR_NOT_SPD
+                                                      ? "Cholesky pivot not positive"
+                                                      : "zero pivot in LU") +
+                                          " at level " + std::to_string(e.level) +
+                                          ", cluster " + std::to_string(e.cluster));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Factorization of one level (all colour classes) -- Alg. 1 inner loop.
+// ---------------------------------------------------------------------------
+template <typename real>
+void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double eps) {
+  const LevelPattern& P = FL.P;
+  const int nc = P.nclu;
+  const bool sym = h->symmetric != 0;
+  std::vector<int> cur(P.m);
+  FL.k.assign(nc, 0);
+  // factor arena: T' (m^2), T'_R^T (m^2, general), Y and XT (m x sum of
+  // neighbour sizes) per cluster, upper bounds from the level-start sizes
+  std::vector<int64_t> oT(nc), oTR(nc, -1), oY(nc), oXT(nc, -1);
+  std::vector<int> wmax(nc, 0);
+  int64_t fe = 0;
+  for (int s = 0; s < nc; s++) {
+    int w = 0;
+    for (int p = P.ptr[s]; p < P.ptr[s + 1]; p++)
+      if (P.kind[p] == 1) w += P.m[P.col[p]];
+    wmax[s] = w;
+    int64_t m = P.m[s];
+    oT[s] = fe;
+    fe += m * m;
+    if (!sym) {
+      oTR[s] = fe;
+      fe += m * m;
+    }
+    oY[s] = fe;
+    fe += m * std::max(w, 1);
+    if (!sym) {
+      oXT[s] = fe;
+      fe += m * std::max(w, 1);
+    }
+    fe = (fe + 3) / 4 * 4;
+  }
+  FL.fac.alloc(std::max<int64_t>(fe, 4) * sizeof(real));
+  h->factor_bytes += FL.fac.bytes;
+  real* fac = FL.fac.as<real>();
+  DevBuf d_rank;
+  d_rank.alloc(sizeof(int) * std::max(nc, 1));
+  {
+    // clusters never processed (m = 0) report rank 0
+    HS_CUDA(cudaMemsetAsync(d_rank.p, 0, sizeof(int) * std::max(nc, 1), h->st));
+  }
+  int* rank = d_rank.as<int>();
+  std::vector<ApplyRec> recs(nc);
+  std::vector<int64_t> vmap;
+  std::vector<int> fillcols(nc, 0), fillw(nc, 0);
+  FL.cls.clear();
+  for (size_t c = 0; c < P.classes.size(); c++) {
+    std::vector<int> S;
+    for (int s : P.classes[c])
+      if (cur[s] > 0) S.push_back(s);
+    if (S.empty()) continue;
+    FL.cls.push_back(S);
+    const int nt = (int)S.size();
+    std::vector<PrepTask> prep(nt);
+    std::vector<GemmTask> gY, gXT, gE, gE2;
+    std::vector<SchurTask> sch;
+    std::vector<ScatterSeg> segN, segW;
+    std::vector<int64_t> gptr;
+    std::vector<int> gstr;
+    std::vector<int> smap;
+    std::vector<int64_t> sbase;
+    std::vector<int> sld;
+    int64_t ws_e = 0, wsd_e = 0;
+    int maxm = 0, maxnw = 0, maxnwf = 0, maxw_seg = 0;
+    for (int t = 0; t < nt; t++) {
+      const int s = S[t];
+      const int m = cur[s];
+      maxm = std::max(maxm, m);
+      struct Nb { int j, w; int64_t p_sj, p_js; };
+      std::vector<Nb> N, W;
+      for (int p = P.ptr[s]; p < P.ptr[s + 1]; p++) {
+        int j = P.col[p];
+        if (j == s || cur[j] == 0) continue;
+        int64_t pj = P.find(j, s);
+        Nb e{j, cur[j], P.off[p], P.off[pj]};
+        if (P.kind[p] == 1) N.push_back(e);
+        else W.push_back(e);
+      }
+      int nw = 0, nwf = 0;
+      for (auto& e : N) nw += e.w;
+      for (auto& e : W) nwf += e.w;
+      fillw[s] = nwf;
+      fillcols[s] = sym ? nwf : 2 * nwf;
+      maxnw = std::max(maxnw, nw);
+      maxnwf = std::max(maxnwf, nwf);
+      // G column descriptors: columns of A_sw, then (general) rows of A_ws
+      const int64_t gcol = (int64_t)gptr.size();
+      for (auto& e : W)
+        for (int q = 0; q < e.w; q++) {
+          gptr.push_back(e.p_sj + (int64_t)q * P.ld[s]);
+          gstr.push_back(1);
+        }
+      if (!sym)
+        for (auto& e : W)
+          for (int q = 0; q < e.w; q++) {
+            gptr.push_back(e.p_js + q);
+            gstr.push_back(P.ld[e.j]);
+          }
+      const int ncolG = sym ? nwf : 2 * nwf;
+      // neighbour column descriptors (A_sN columns, then rows of A_Ns)
+      const int64_t ncol0 = (int64_t)gptr.size();
+      for (auto& e : N)
+        for (int q = 0; q < e.w; q++) {
+          gptr.push_back(e.p_sj + (int64_t)q * P.ld[s]);
+          gstr.push_back(1);
+        }
+      const int64_t ncol1 = (int64_t)gptr.size();
+      if (!sym)
+        for (auto& e : N)
+          for (int q = 0; q < e.w; q++) {
+            gptr.push_back(e.p_js + q);
+            gstr.push_back(P.ld[e.j]);
+          }
+      // workspace
+      const int64_t mm = (int64_t)m * m;
+      PrepTask& pt = prep[t];
+      pt.s = s;
+      pt.m = m;
+      pt.ld = P.ld[s];
+      pt.ncolG = ncolG;
+      pt.a_ss = P.off[P.find(s, s)];
+      pt.gcol = gcol;
+      pt.ws = ws_e;
+      ws_e += 11 * mm + (int64_t)m * ncolG;
+      pt.D = ws_e;
+      ws_e += mm;
+      pt.D2 = ws_e;
+      ws_e += mm;
+      int64_t Eoff = ws_e;
+      ws_e += (int64_t)m * std::max(nwf, 1);
+      int64_t E2off = ws_e;
+      if (!sym) ws_e += (int64_t)m * std::max(nwf, 1);
+      ws_e = (ws_e + 3) / 4 * 4;
+      pt.wsd = wsd_e;
+      wsd_e += 2 * (int64_t)ncolG + 3 * m + 8;
+      pt.T = oT[s];
+      pt.TR = sym ? oT[s] : oTR[s];
+      // Y = T' A_sN  (rows 0..k coarse rows, rows k.. = B_R)
+      if (nw > 0) {
+        GemmTask g{};
+        g.s = s; g.M = m; g.N = nw; g.K = m; g.mode = 0; g.lda = m; g.ldc = m;
+        g.A = oT[s]; g.C = oY[s]; g.bcol = ncol0;
+        gY.push_back(g);
+        if (!sym) {
+          g.A = oTR[s]; g.C = oXT[s]; g.bcol = ncol1;
+          gXT.push_back(g);
+        }
+      }
+      // E = D A_sW (coarse-to-far rows), E2 = D2 A_wsT (far-to-coarse cols)
+      if (nwf > 0) {
+        GemmTask g{};
+        g.s = s; g.M = m; g.N = nwf; g.K = m; g.mode = 1; g.lda = m; g.ldc = m;
+        g.A = pt.D; g.C = Eoff; g.bcol = gcol;
+        gE.push_back(g);
+        if (!sym) {
+          g.A = pt.D2; g.C = E2off; g.bcol = gcol + nwf;
+          gE2.push_back(g);
+        }
+      }
+      // scatter segments
+      int c0 = 0;
+      for (auto& e : N) {
+        ScatterSeg sg{};
+        sg.s = s; sg.width = e.w; sg.ld_s = P.ld[s]; sg.ld_o = P.ld[e.j];
+        sg.src = oY[s] + (int64_t)c0 * m;
+        sg.src2 = sym ? -1 : oXT[s] + (int64_t)c0 * m;
+        sg.ld_src = m; sg.m = m;
+        sg.dst_row = e.p_sj; sg.dst_col = e.p_js;
+        segN.push_back(sg);
+        maxw_seg = std::max(maxw_seg, e.w);
+        c0 += e.w;
+      }
+      c0 = 0;
+      for (auto& e : W) {
+        ScatterSeg sg{};
+        sg.s = s; sg.width = e.w; sg.ld_s = P.ld[s]; sg.ld_o = P.ld[e.j];
+        sg.src = Eoff + (int64_t)c0 * m;
+        sg.src2 = sym ? -1 : E2off + (int64_t)c0 * m;
+        sg.ld_src = m; sg.m = m;
+        sg.dst_row = e.p_sj; sg.dst_col = e.p_js;
+        segW.push_back(sg);
+        maxw_seg = std::max(maxw_seg, e.w);
+        c0 += e.w;
+      }
+      // Schur task: maps and block bases
+      if (nw > 0) {
+        SchurTask sc{};
+        sc.s = s; sc.m = m; sc.nw = nw; sc.nb = (int)N.size();
+        sc.P = sym ? oY[s] : oXT[s];
+        sc.Q = oY[s];
+        sc.map = (int64_t)smap.size();
+        for (int a = 0; a < (int)N.size(); a++)
+          for (int q = 0; q < N[a].w; q++) smap.push_back((a << 20) | q);
+        sc.base = (int64_t)sbase.size();
+        for (int a = 0; a < (int)N.size(); a++)
+          for (int b = 0; b < (int)N.size(); b++) {
+            int64_t p = P.find(N[a].j, N[b].j);
+            if (p < 0) throw Fail(HSOLVE_ERR_CUDA, "internal: missing Schur target block");
+            sbase.push_back(P.off[p]);
+          }
+        sc.ldn = (int64_t)sld.size();
+        for (auto& e : N) sld.push_back(P.ld[e.j]);
+        sch.push_back(sc);
+      }
+      // apply record (k filled after the class completes)
+      ApplyRec& r = recs[s];
+      r.m = m; r.k = 0; r.nw = nw; r.sym = sym ? 1 : 0;
+      r.voff = P.voff[s];
+      r.T = oT[s]; r.TR = sym ? oT[s] : oTR[s];
+      r.Y = oY[s]; r.XT = sym ? oY[s] : oXT[s];
+      r.map = (int64_t)vmap.size();
+      for (auto& e : N)
+        for (int q = 0; q < e.w; q++) vmap.push_back(P.voff[e.j] + q);
+    }
+    // ---- upload this class's task arrays
+    Blob b;
+    size_t o_prep = b.add(prep), o_gY = b.add(gY), o_gXT = b.add(gXT), o_gE = b.add(gE),
+           o_gE2 = b.add(gE2), o_sch = b.add(sch), o_segN = b.add(segN), o_segW = b.add(segW),
+           o_gptr = b.add(gptr), o_gstr = b.add(gstr), o_smap = b.add(smap),
+           o_sbase = b.add(sbase), o_sld = b.add(sld);
+    h->ws.ensure(std::max<int64_t>(ws_e, 4) * sizeof(real));
+    h->wsd.ensure(std::max<int64_t>(wsd_e, 4) * sizeof(double));
+    char* d = upload_blob(h, b);
+    real* ws = h->ws.as<real>();
+    const int64_t* d_gptr = reinterpret_cast<const int64_t*>(d + o_gptr);
+    const int* d_gstr = reinterpret_cast<const int*>(d + o_gstr);
+    timed(h, "prep", 1, [&] {
+      Launch<real>::prep(reinterpret_cast<const PrepTask*>(d + o_prep), nt, arena, fac, ws,
+                         h->wsd.as<double>(), d_gptr, d_gstr, rank, eps, sym ? 1 : 0,
+                         h->opts.max_rank, maxm, h->d_err.as<DevError>(), level, h->st);
+    });
+    timed(h, "gemm_coarse", sym ? 1 : 2, [&] {
+      Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gY), (int)gY.size(), maxm,
+                                maxnw, fac, fac, arena, d_gptr, d_gstr, rank, h->st);
+      if (!sym)
+        Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gXT), (int)gXT.size(),
+                                  maxm, maxnw, fac, fac, arena, d_gptr, d_gstr, rank, h->st);
+    });
+    timed(h, "gemm_fill", sym ? 1 : 2, [&] {
+      Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gE), (int)gE.size(), maxm,
+                                maxnwf, ws, ws, arena, d_gptr, d_gstr, rank, h->st);
+      if (!sym)
+        Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gE2), (int)gE2.size(),
+                                  maxm, maxnwf, ws, ws, arena, d_gptr, d_gstr, rank, h->st);
+    });
+    timed(h, "scatter", 2, [&] {
+      Launch<real>::scatter(reinterpret_cast<const ScatterSeg*>(d + o_segN), (int)segN.size(),
+                            maxw_seg, fac, arena, rank, h->st);
+      Launch<real>::scatter(reinterpret_cast<const ScatterSeg*>(d + o_segW), (int)segW.size(),
+                            maxw_seg, ws, arena, rank, h->st);
+    });
+    timed(h, "schur", 1, [&] {
+      Launch<real>::schur(reinterpret_cast<const SchurTask*>(d + o_sch), (int)sch.size(), maxnw,
+                          fac, arena, reinterpret_cast<const int*>(d + o_smap),
+                          reinterpret_cast<const int64_t*>(d + o_sbase),
+                          reinterpret_cast<const int*>(d + o_sld), rank, h->st);
+    });
+    // ---- ranks of this class (the next class's neighbour widths need them)
+    std::vector<int> kk(nc);
+    HS_CUDA(cudaMemcpyAsync(kk.data(), rank, sizeof(int) * nc, cudaMemcpyDeviceToHost, h->st));
+    check_dev_error(h);  // synchronises the stream
+    for (int s : S) {
+      FL.k[s] = kk[s];
+      cur[s] = kk[s];
+      recs[s].k = kk[s];
+      const int m = recs[s].m, k = kk[s], f = m - k;
+      const int nw = recs[s].nw;
+      // algorithmic flops: dense per-cluster work + the batched products
+      double mf = m;
+      if (k < m) {
+        // per-cluster dense work: Cholesky m^3/3 (+ its inverse m^3/3 for
+        // k = 0); with fill: inverse m^3, pivoted QR 4 m c k, complement
+        // 4 m^2 k, T 2 m^3, F and C 2 m^2 m, L_F^{-1} T 2 f^2 m
+        double pf = 2.0 / 3.0 * mf * mf * mf;
+        if (k > 0)
+          pf = mf * mf * mf / 3.0 + mf * mf * mf + 4.0 * mf * fillcols[s] * k +
+               4.0 * mf * mf * k + 2.0 * mf * mf * mf + 2.0 * mf * mf * mf +
+               2.0 * (double)f * f * mf;
+        double gf = 2.0 * mf * mf * nw * (sym ? 1 : 2) +
+                    (k > 0 ? 2.0 * k * mf * fillw[s] * (sym ? 1 : 2) : 0.0);
+        double sf = 2.0 * f * (double)nw * nw;
+        h->prep_flops += pf;
+        h->gemm_flops += gf;
+        h->schur_flops += sf;
+        h->factor_flops += pf + gf + sf;
+        // operators: T' and B_R each read by both sweeps (SPD), or T', T_R',
+        // B_L, B_R each read once (general): 2 (m^2 + f nw) words either way
+        h->apply_bytes += (int64_t)sizeof(real) * 2 * ((int64_t)m * m + (int64_t)f * nw);
+        h->apply_bytes += (int64_t)sizeof(real) * 2 * (2 * (int64_t)m + 2 * (int64_t)nw);
+      }
+    }
+  }
+  // ---- apply records and maps for this level
+  Blob b;
+  FL.recs.alloc(sizeof(ApplyRec) * std::max(nc, 1));
+  HS_CUDA(cudaMemcpyAsync(FL.recs.p, recs.data(), sizeof(ApplyRec) * nc, cudaMemcpyHostToDevice,
+                          h->st));
+  FL.vmap.alloc(sizeof(int64_t) * std::max<size_t>(vmap.size(), 1));
+  if (!vmap.empty())
+    HS_CUDA(cudaMemcpyAsync(FL.vmap.p, vmap.data(), sizeof(int64_t) * vmap.size(),
+                            cudaMemcpyHostToDevice, h->st));
+  std::vector<int> ids;
+  FL.cls_off.clear();
+  FL.cls_maxm.clear();
+  for (auto& S : FL.cls) {
+    FL.cls_off.push_back((int)ids.size());
+    int mx = 1;
+    for (int s : S) {
+      ids.push_back(s);
+      mx = std::max(mx, std::max(recs[s].m, recs[s].nw));
+    }
+    FL.cls_maxm.push_back(mx);
+  }
+  FL.cls_off.push_back((int)ids.size());
+  FL.ids.alloc(sizeof(int) * std::max<size_t>(ids.size(), 1));
+  if (!ids.empty())
+    HS_CUDA(cudaMemcpyAsync(FL.ids.p, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice,
+                            h->st));
+  HS_CUDA(cudaStreamSynchronize(h->st));
+  h->colours_total += (int)FL.cls.size();
+}
+
+// Next level (Alg. 1 recursion): cluster I holds the coarse unknowns of
+// clusters 2I and 2I+1 (left first); the block pattern is the set of child
+// pairs that were within distance two and both kept coarse unknowns.  With
+// `to_top`, every live cluster merges into one (dense top factor).
+template <typename real>
+void build_next(hsolve_handle* h, FLevel& FL, const real* arena, std::unique_ptr<FLevel>& out,
+                DevBuf& out_arena, bool to_top, const std::vector<int>& kin) {
+  const LevelPattern& P = FL.P;
+  const int nc = P.nclu;
+  out.reset(new FLevel());
+  LevelPattern& Q = out->P;
+  auto parent = [&](int a) { return to_top ? 0 : a / 2; };
+  Q.nclu = to_top ? 1 : nc / 2;
+  Q.m.assign(Q.nclu, 0);
+  std::vector<int> ro(nc, 0);  // row offset of child a inside its parent
+  for (int a = 0; a < nc; a++) {
+    int I = parent(a);
+    ro[a] = Q.m[I];
+    Q.m[I] += kin[a];
+  }
+  std::vector<std::vector<int>> adj(Q.nclu);
+  for (int a = 0; a < nc; a++) {
+    if (kin[a] == 0) continue;
+    for (int p = P.ptr[a]; p < P.ptr[a + 1]; p++) {
+      int b = P.col[p];
+      if (kin[b] == 0) continue;
+      int I = parent(a), J = parent(b);
+      if (I != J) adj[I].push_back(J);
+    }
+  }
+  for (auto& v : adj) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  }
+  build_level_pattern(Q, adj);
+  out_arena.alloc(Q.arena_elems * sizeof(real));
+  HS_CUDA(cudaMemsetAsync(out_arena.p, 0, Q.arena_elems * sizeof(real), h->st));
+  std::vector<CopyTask> tasks;
+  for (int a = 0; a < nc; a++) {
+    if (kin[a] == 0) continue;
+    for (int p = P.ptr[a]; p < P.ptr[a + 1]; p++) {
+      int b = P.col[p];
+      if (kin[b] == 0) continue;
+      int I = parent(a), J = parent(b);
+      int64_t q = Q.find(I, J);
+      if (q < 0) throw Fail(HSOLVE_ERR_CUDA, "internal: missing next-level block");
+      CopyTask t;
+      t.rows = kin[a];
+      t.cols = kin[b];
+      t.ld_src = P.ld[a];
+      t.ld_dst = Q.ld[I];
+      t.src = P.off[p];
+      t.dst = Q.off[q] + ro[a] + (int64_t)ro[b] * Q.ld[I];
+      tasks.push_back(t);
+    }
+  }
+  if (!tasks.empty()) {
+    Blob bl;
+    size_t o = bl.add(tasks);
+    char* d = upload_blob(h, bl);
+    timed(h, "assemble", 1, [&] {
+      Launch<real>::copy_blocks(reinterpret_cast<const CopyTask*>(d + o), (int)tasks.size(), arena,
+                                out_arena.as<real>(), h->st);
+    });
+  }
+  // vector gather map: next-level position -> this level's position
+  std::vector<int64_t> idx;
+  for (int I = 0; I < Q.nclu; I++)
+    for (int a = 0; a < nc; a++)
+      if (parent(a) == I)
+        for (int i = 0; i < kin[a]; i++) idx.push_back(P.voff[a] + i);
+  FL.next_n = (int64_t)idx.size();
+  FL.next_idx.alloc(sizeof(int64_t) * std::max<size_t>(idx.size(), 1));
+  if (!idx.empty())
+    HS_CUDA(cudaMemcpyAsync(FL.next_idx.p, idx.data(), sizeof(int64_t) * idx.size(),
+                            cudaMemcpyHostToDevice, h->st));
+  HS_CUDA(cudaStreamSynchronize(h->st));
+}
+
+template <typename real>
+void factor_impl(hsolve_handle* h, double eps) {
+  h->F.clear();
+  h->factor_flops = h->schur_flops = h->prep_flops = h->gemm_flops = 0;
+  h->apply_bytes = h->factor_bytes = h->block_bytes = 0;
+  h->launches = 0;
+  h->colours_total = 0;
+  h->coarse_total = 0;
+  h->phases.clear();
+  HS_CUDA(cudaMemsetAsync(h->d_err.p, 0, sizeof(DevError), h->st));
+  cudaEvent_t e0, e1;
+  HS_CUDA(cudaEventCreate(&e0));
+  HS_CUDA(cudaEventCreate(&e1));
+  HS_CUDA(cudaEventRecord(e0, h->st));
+  // level-0 blocks from the CSR values
+  std::unique_ptr<FLevel> cur(new FLevel());
+  cur->P = h->L0;
+  DevBuf arena;
+  arena.alloc(cur->P.arena_elems * sizeof(real));
+  HS_CUDA(cudaMemsetAsync(arena.p, 0, cur->P.arena_elems * sizeof(real), h->st));
+  timed(h, "upload", 1, [&] {
+    Launch<real>::scatter_csr(h->d_csr_dst.as<int64_t>(), h->d_val.as<double>(), h->nnz,
+                              arena.as<real>(), h->st);
+  });
+  int level = 0;
+  while (true) {
+    LevelPattern& P = cur->P;
+    h->block_bytes = std::max<int64_t>(h->block_bytes, (int64_t)arena.bytes);
+    int live = 0;
+    for (int i = 0; i < P.nclu; i++) live += P.m[i] > 0;
+    const int64_t vlen = P.voff[P.nclu];
+    const bool small = (P.nclu == 1 || live <= 1 || vlen <= h->opts.top_size);
+    if (small && !(P.nclu == 1)) {
+      // merge everything into one cluster for the dense top factor
+      std::unique_ptr<FLevel> nxt;
+      DevBuf narena;
+      std::vector<int> kin(P.m.begin(), P.m.end());
+      build_next<real>(h, *cur, arena.as<real>(), nxt, narena, true, kin);
+      // the merge level itself has no factors: mark it as a pass-through
+      cur->cls.clear();
+      cur->cls_off.assign(1, 0);
+      cur->k = kin;
+      cur->recs.alloc(16);
+      cur->vmap.alloc(16);
+      cur->ids.alloc(16);
+      h->F.push_back(std::move(cur));
+      cur = std::move(nxt);
+      arena = std::move(narena);
+      level++;
+      continue;
+    }
+    factor_level<real>(h, *cur, arena.as<real>(), level, eps);
+    for (int i = 0; i < P.nclu; i++) h->coarse_total += cur->k[i];
+    if (P.nclu == 1) {
+      cur->top = true;
+      h->F.push_back(std::move(cur));
+      break;
+    }
+    std::unique_ptr<FLevel> nxt;
+    DevBuf narena;
+    std::vector<int> kin = cur->k;
+    build_next<real>(h, *cur, arena.as<real>(), nxt, narena, false, kin);
+    h->F.push_back(std::move(cur));
+    cur = std::move(nxt);
+    arena = std::move(narena);
+    level++;
+  }
+  HS_CUDA(cudaEventRecord(e1, h->st));
+  HS_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->factor_ms = ms;
+}
+
+// ---------------------------------------------------------------------------
+// Substitution (Alg. 2)
+// ---------------------------------------------------------------------------
+template <typename real>
+void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int64_t ld) {
+  const int L = (int)h->F.size();
+  for (auto& F : h->F) {
+    size_t need = sizeof(real) * (size_t)std::max<int64_t>(F->P.voff[F->P.nclu], 1) * nrhs;
+    if (F->vec.bytes < need) F->vec.alloc(need);
+  }
+  FLevel& F0 = *h->F[0];
+  const int64_t n0 = F0.P.voff[F0.P.nclu];
+  Launch<real>::perm_in(h->d_perm.as<int64_t>(), h->n, rhs, ld, F0.vec.as<real>(), n0, nrhs, h->st);
+  for (int l = 0; l < L; l++) {
+    FLevel& F = *h->F[l];
+    const int64_t nl = std::max<int64_t>(F.P.voff[F.P.nclu], 1);
+    for (size_t c = 0; c < F.cls.size(); c++)
+      Launch<real>::apply_fwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
+                              (int)F.cls[c].size(), F.fac.as<real>(), F.vmap.as<int64_t>(),
+                              F.vec.as<real>(), nl, nrhs, F.cls_maxm[c], h->st);
+    if (l + 1 < L) {
+      FLevel& G = *h->F[l + 1];
+      const int64_t ng = std::max<int64_t>(G.P.voff[G.P.nclu], 1);
+      Launch<real>::gather_vec(F.next_idx.as<int64_t>(), F.next_n, F.vec.as<real>(), nl,
+                               G.vec.as<real>(), ng, nrhs, h->st);
+    }
+  }
+  for (int l = L - 1; l >= 0; l--) {
+    FLevel& F = *h->F[l];
+    const int64_t nl = std::max<int64_t>(F.P.voff[F.P.nclu], 1);
+    if (l + 1 < L) {
+      FLevel& G = *h->F[l + 1];
+      const int64_t ng = std::max<int64_t>(G.P.voff[G.P.nclu], 1);
+      Launch<real>::scatter_vec(F.next_idx.as<int64_t>(), F.next_n, G.vec.as<real>(), ng,
+                                F.vec.as<real>(), nl, nrhs, h->st);
+    }
+    for (int c = (int)F.cls.size() - 1; c >= 0; c--)
+      Launch<real>::apply_bwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
+                              (int)F.cls[c].size(), F.fac.as<real>(), F.vmap.as<int64_t>(),
+                              F.vec.as<real>(), nl, nrhs, F.cls_maxm[c], h->st);
+  }
+  Launch<real>::perm_out(h->d_perm.as<int64_t>(), h->n, F0.vec.as<real>(), n0, out, ld, nrhs, h->st);
+}
+
+void apply_any(hsolve_handle* h, const double* rhs, double* out, int nrhs, int64_t ld) {
+  if (h->prec == HSOLVE_FP64)
+    apply_impl<double>(h, rhs, out, nrhs, ld);
+  else
+    apply_impl<float>(h, rhs, out, nrhs, ld);
+}
+
+// ---------------------------------------------------------------------------
+// Krylov solvers (float64)
+// ---------------------------------------------------------------------------
+struct Scalars {  // device scratch for dot products
+  double* part;
+  double* res;
+};
+
+// out[c] = a[:,c].b[:,c] for c < nrhs, copied to host vector
+void dots_host(hsolve_handle* h, const double* a, const double* b, int64_t ld, int nrhs,
+               std::vector<double>& out) {
+  const int kDotBlocks = 256;
+  h->dots.ensure(sizeof(double) * (size_t)(nrhs + 64) * (kDotBlocks + 1));
+  double* d = h->dots.as<double>();
+  hs::dots(h->n, a, ld, b, ld, nrhs, d, h->st);
+  out.resize(nrhs);
+  h->pin_small.ensure(sizeof(double) * (nrhs + 64) * 2);
+  HS_CUDA(cudaMemcpyAsync(h->pin_small.p, d + (int64_t)nrhs * kDotBlocks, sizeof(double) * nrhs,
+                          cudaMemcpyDeviceToHost, h->st));
+  HS_CUDA(cudaStreamSynchronize(h->st));
+  std::memcpy(out.data(), h->pin_small.p, sizeof(double) * nrhs);
+}
+
+void upload_coefs(hsolve_handle* h, const std::vector<double>& v, double* dst) {
+  h->pin_small.ensure(sizeof(double) * (v.size() + 64) * 2);
+  double* p = reinterpret_cast<double*>(h->pin_small.p) + 64 + v.size();
+  // the pinned area is reused: wait for the previous copy out of it
+  HS_CUDA(cudaStreamSynchronize(h->st));
+  std::memcpy(p, v.data(), sizeof(double) * v.size());
+  HS_CUDA(cudaMemcpyAsync(dst, p, sizeof(double) * v.size(), cudaMemcpyHostToDevice, h->st));
+}
+
+hsolve_status pcg_impl(hsolve_handle* h, double tol, int maxit, const double* b, double* x,
+                       int nrhs, int64_t ldx, hsolve_solve_info* info) {
+  const int64_t n = h->n;
+  // vectors: r, z, p, q (n x nrhs each, ld n) + coefficient arrays
+  h->kry.ensure(sizeof(double) * ((size_t)4 * n * nrhs + 8 * (size_t)nrhs + 64));
+  double* r = h->kry.as<double>();
+  double* z = r + n * nrhs;
+  double* p = z + n * nrhs;
+  double* q = p + n * nrhs;
+  double* coef = q + n * nrhs;  // [alpha | -alpha | one | beta | zero] per rhs
+  std::vector<double> bb, rr, rz, pq;
+  dots_host(h, b, b, ldx, nrhs, bb);  // b uses ldx
+  // x = 0, r = b
+  for (int c = 0; c < nrhs; c++) {
+    HS_CUDA(cudaMemsetAsync(x + c * ldx, 0, sizeof(double) * n, h->st));
+    HS_CUDA(cudaMemcpyAsync(r + c * n, b + c * ldx, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                            h->st));
+  }
+  std::vector<double> nb(nrhs);
+  for (int c = 0; c < nrhs; c++) nb[c] = std::sqrt(bb[c]);
+  apply_any(h, r, z, nrhs, n);
+  HS_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, h->st));
+  dots_host(h, r, z, n, nrhs, rz);
+  std::vector<char> done(nrhs, 0);
+  for (int c = 0; c < nrhs; c++) done[c] = (nb[c] == 0.0);
+  int it = 0;
+  std::vector<double> res(nrhs, 0.0);
+  bool all = std::all_of(done.begin(), done.end(), [](char d) { return d != 0; });
+  std::vector<double> ones(nrhs, 1.0), cf(nrhs), cm(nrhs);
+  while (!all && it < maxit) {
+    it++;
+    spmv_csr(n, h->d_rowptr.as<int64_t>(), h->d_col.as<int>(), h->d_val.as<double>(), p, n, q, n,
+             nrhs, h->st);
+    dots_host(h, p, q, n, nrhs, pq);
+    for (int c = 0; c < nrhs; c++) {
+      double a = (done[c] || pq[c] == 0.0) ? 0.0 : rz[c] / pq[c];
+      cf[c] = a;
+      cm[c] = -a;
+    }
+    // x += a p ; r -= a q
+    upload_coefs(h, cf, coef);
+    upload_coefs(h, ones, coef + 2 * nrhs);
+    axpby_cols(n, nrhs, coef, p, n, coef + 2 * nrhs, x, ldx, h->st);
+    upload_coefs(h, cm, coef + nrhs);
+    axpby_cols(n, nrhs, coef + nrhs, q, n, coef + 2 * nrhs, r, n, h->st);
+    dots_host(h, r, r, n, nrhs, rr);
+    for (int c = 0; c < nrhs; c++) {
+      res[c] = std::sqrt(rr[c]) / (nb[c] > 0 ? nb[c] : 1.0);
+      if (!done[c] && res[c] <= tol) done[c] = 1;
+    }
+    all = std::all_of(done.begin(), done.end(), [](char d) { return d != 0; });
+    if (all) break;
+    apply_any(h, r, z, nrhs, n);
+    std::vector<double> rzn;
+    dots_host(h, r, z, n, nrhs, rzn);
+    for (int c = 0; c < nrhs; c++) {
+      cf[c] = (done[c] || rz[c] == 0.0) ? 0.0 : rzn[c] / rz[c];
+      rz[c] = rzn[c];
+    }
+    // p = z + beta p
+    upload_coefs(h, cf, coef + 3 * nrhs);
+    axpby_cols(n, nrhs, coef + 2 * nrhs, z, n, coef + 3 * nrhs, p, n, h->st);
+  }
+  // true residual b - A x
+  spmv_csr(n, h->d_rowptr.as<int64_t>(), h->d_col.as<int>(), h->d_val.as<double>(), x, ldx, q, n,
+           nrhs, h->st);
+  for (int c = 0; c < nrhs; c++) cm[c] = -1.0;
+  upload_coefs(h, cm, coef + nrhs);
+  for (int c = 0; c < nrhs; c++)
+    HS_CUDA(cudaMemcpyAsync(r + c * n, b + c * ldx, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                            h->st));
+  axpby_cols(n, nrhs, coef + 2 * nrhs, r, n, coef + nrhs, q, n, h->st);  // q = r - q
+  dots_host(h, q, q, n, nrhs, rr);
+  double worst = 0;
+  for (int c = 0; c < nrhs; c++)
+    worst = std::max(worst, nb[c] > 0 ? std::sqrt(rr[c]) / nb[c] : 0.0);
+  if (info) {
+    info->iterations = it;
+    info->rel_residual = worst;
+  }
+  if (worst > tol) return HSOLVE_ERR_NO_CONVERGENCE;
+  return HSOLVE_OK;
+}
+
+// Right-preconditioned flexible GMRES(restart) with CGS2, one right-hand side
+// at a time.
+hsolve_status fgmres_one(hsolve_handle* h, double tol, int maxit, const double* b, double* x,
+                         int restart, int* iters, double* relres) {
+  const int64_t n = h->n;
+  const int R = restart;
+  h->kry.ensure(sizeof(double) * ((size_t)(2 * R + 3) * n + 4 * (size_t)R + 256));
+  double* V = h->kry.as<double>();          // n x (R+1)
+  double* Z = V + (int64_t)(R + 1) * n;     // n x R
+  double* w = Z + (int64_t)R * n;           // n
+  double* coef = w + n;                     // R+1
+  std::vector<double> tmp;
+  dots_host(h, b, b, n, 1, tmp);
+  const double nb = std::sqrt(tmp[0]);
+  HS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, h->st));
+  if (nb == 0.0) {
+    *iters = 0;
+    *relres = 0;
+    return HSOLVE_OK;
+  }
+  int total = 0;
+  double res = 1.0;
+  std::vector<double> one{1.0}, mone{-1.0};
+  while (total < maxit) {
+    // r = b - A x into V[:,0]
+    spmv_csr(n, h->d_rowptr.as<int64_t>(), h->d_col.as<int>(), h->d_val.as<double>(), x, n, w, n,
+             1, h->st);
+    HS_CUDA(cudaMemcpyAsync(V, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+    upload_coefs(h, one, coef);
+    upload_coefs(h, mone, coef + 1);
+    axpby_cols(n, 1, coef + 1, w, n, coef, V, n, h->st);  // V0 = -w + V0
+    dots_host(h, V, V, n, 1, tmp);
+    double beta = std::sqrt(tmp[0]);
+    res = beta / nb;
+    if (res <= tol) break;
+    std::vector<double> sc{1.0 / beta}, zero{0.0};
+    upload_coefs(h, sc, coef);
+    upload_coefs(h, zero, coef + 1);
+    axpby_cols(n, 1, coef, V, n, coef + 1, V, n, h->st);
+    std::vector<std::vector<double>> H(R + 1, std::vector<double>(R, 0.0));
+    std::vector<double> cs(R), sn(R), g(R + 1, 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < R; j++) {
+      apply_any(h, V + (int64_t)j * n, Z + (int64_t)j * n, 1, n);
+      spmv_csr(n, h->d_rowptr.as<int64_t>(), h->d_col.as<int>(), h->d_val.as<double>(),
+               Z + (int64_t)j * n, n, w, n, 1, h->st);
+      std::vector<double> hcol(j + 1, 0.0);
+      for (int pass = 0; pass < 2; pass++) {
+        h->dots.ensure(sizeof(double) * (size_t)(R + 64) * 257);
+        double* d = h->dots.as<double>();
+        multi_dot(n, j + 1, V, n, w, d, h->st);
+        std::vector<double> hh(j + 1);
+        h->pin_small.ensure(sizeof(double) * (R + 64) * 4);
+        HS_CUDA(cudaMemcpyAsync(h->pin_small.p, d + (int64_t)(j + 1) * 256,
+                                sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, h->st));
+        HS_CUDA(cudaStreamSynchronize(h->st));
+        std::memcpy(hh.data(), h->pin_small.p, sizeof(double) * (j + 1));
+        upload_coefs(h, hh, coef);
+        multi_axpy(n, j + 1, V, n, coef, -1.0, w, h->st);
+        for (int i = 0; i <= j; i++) hcol[i] += hh[i];
+      }
+      dots_host(h, w, w, n, 1, tmp);
+      double hn = std::sqrt(tmp[0]);
+      for (int i = 0; i <= j; i++) H[i][j] = hcol[i];
+      H[j + 1][j] = hn;
+      if (hn > 0) {
+        std::vector<double> sc2{1.0 / hn}, z2{0.0};
+        upload_coefs(h, sc2, coef);
+        upload_coefs(h, z2, coef + 1);
+        HS_CUDA(cudaMemcpyAsync(V + (int64_t)(j + 1) * n, w, sizeof(double) * n,
+                                cudaMemcpyDeviceToDevice, h->st));
+        axpby_cols(n, 1, coef, V + (int64_t)(j + 1) * n, n, coef + 1, V + (int64_t)(j + 1) * n, n,
+                   h->st);
+      }
+      for (int i = 0; i < j; i++) {
+        double t = cs[i] * H[i][j] + sn[i] * H[i + 1][j];
+        H[i + 1][j] = -sn[i] * H[i][j] + cs[i] * H[i + 1][j];
+        H[i][j] = t;
+      }
+      double den = std::hypot(H[j][j], H[j + 1][j]);
+      cs[j] = den > 0 ? H[j][j] / den : 1.0;
+      sn[j] = den > 0 ? H[j + 1][j] / den : 0.0;
+      H[j][j] = den;
+      H[j + 1][j] = 0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      total++;
+      jdone = j + 1;
+      if (std::fabs(g[j + 1]) <= tol * nb || total >= maxit) break;
+    }
+    // y = H^{-1} g, x += Z y
+    std::vector<double> y(jdone);
+    for (int i = jdone - 1; i >= 0; i--) {
+      double s = g[i];
+      for (int l = i + 1; l < jdone; l++) s -= H[i][l] * y[l];
+      y[i] = s / H[i][i];
+    }
+    upload_coefs(h, y, coef);
+    multi_axpy(n, jdone, Z, n, coef, 1.0, x, h->st);
+  }
+  // final true residual
+  spmv_csr(n, h->d_rowptr.as<int64_t>(), h->d_col.as<int>(), h->d_val.as<double>(), x, n, w, n, 1,
+           h->st);
+  HS_CUDA(cudaMemcpyAsync(V, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  upload_coefs(h, one, coef);
+  upload_coefs(h, mone, coef + 1);
+  axpby_cols(n, 1, coef + 1, w, n, coef, V, n, h->st);
+  dots_host(h, V, V, n, 1, tmp);
+  res = std::sqrt(tmp[0]) / nb;
+  *iters = total;
+  *relres = res;
+  return res <= tol ? HSOLVE_OK : HSOLVE_ERR_NO_CONVERGENCE;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+void hsolve_default_opts(hsolve_opts* o) {
+  if (!o) return;
+  o->leaf_size = 128;
+  o->symmetric = -1;
+  o->top_size = 0;
+  o->max_rank = 0;
+  o->gmres_restart = 50;
+}
+
+hsolve_status hsolve_analyze(const hsolve_csr* A, const double* coords, int dim,
+                             const hsolve_opts* opts, void* cuda_stream, hsolve_handle** out) {
+  if (!out) return HSOLVE_ERR_ARG;
+  *out = nullptr;
+  if (!A || A->n <= 0 || A->nnz < 0 || !A->rowptr || !A->col || !A->val) return HSOLVE_ERR_ARG;
+  if (coords && (dim < 1 || dim > 3)) return HSOLVE_ERR_ARG;
+  const int64_t n = A->n;
+  if (A->rowptr[0] != 0 || A->rowptr[n] != A->nnz) return HSOLVE_ERR_ARG;
+  for (int64_t i = 0; i < n; i++)
+    if (A->rowptr[i + 1] < A->rowptr[i]) return HSOLVE_ERR_ARG;
+  for (int64_t p = 0; p < A->nnz; p++)
+    if (A->col[p] < 0 || A->col[p] >= n) return HSOLVE_ERR_ARG;
+  std::unique_ptr<hsolve_handle> h(new hsolve_handle());
+  hsolve_default_opts(&h->opts);
+  if (opts) h->opts = *opts;
+  if (h->opts.leaf_size < 1) return HSOLVE_ERR_ARG;
+  if (h->opts.gmres_restart < 1) h->opts.gmres_restart = 50;
+  h->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  h->n = n;
+  h->nnz = A->nnz;
+  h->rowptr.assign(A->rowptr, A->rowptr + n + 1);
+  h->col.assign(A->col, A->col + A->nnz);
+  h->val.assign(A->val, A->val + A->nnz);
+  try {
+    // exact value symmetry check (symmetric = -1)
+    if (h->opts.symmetric < 0) {
+      bool symm = true;
+      for (int64_t i = 0; i < n && symm; i++)
+        for (int64_t p = h->rowptr[i]; p < h->rowptr[i + 1] && symm; p++) {
+          int64_t j = h->col[p];
+          double v = h->val[p];
+          // find (j, i)
+          auto b = h->col.begin() + h->rowptr[j], e = h->col.begin() + h->rowptr[j + 1];
+          bool found = false;
+          for (auto it = b; it != e; ++it)
+            if (*it == i) {
+              found = (h->val[it - h->col.begin()] == v);
+              break;
+            }
+          if (!found) symm = false;
+        }
+      h->symmetric = symm ? 1 : 0;
+    } else {
+      h->symmetric = h->opts.symmetric ? 1 : 0;
+    }
+    // clusters
+    std::vector<std::vector<int64_t>> leaves;
+    rcb_leaves(n, coords, dim, h->opts.leaf_size, leaves);
+    const int nc = (int)leaves.size();
+    std::vector<int> clu(n);
+    std::vector<int> loc(n);
+    h->perm.clear();
+    for (int i = 0; i < nc; i++) {
+      for (size_t q = 0; q < leaves[i].size(); q++) {
+        clu[leaves[i][q]] = i;
+        loc[leaves[i][q]] = (int)q;
+        h->perm.push_back(leaves[i][q]);
+      }
+    }
+    LevelPattern& L = h->L0;
+    L.nclu = nc;
+    L.m.resize(nc);
+    for (int i = 0; i < nc; i++) L.m[i] = (int)leaves[i].size();
+    h->adj0.assign(nc, {});
+    for (int64_t i = 0; i < n; i++)
+      for (int64_t p = h->rowptr[i]; p < h->rowptr[i + 1]; p++) {
+        int a = clu[i], b = clu[h->col[p]];
+        if (a != b) h->adj0[a].push_back(b);
+      }
+    for (int i = 0; i < nc; i++) {
+      // A_B is made symmetric in structure: a nonzero (i,j) or (j,i) couples
+      for (int j : std::vector<int>(h->adj0[i])) h->adj0[j].push_back(i);
+    }
+    for (auto& v : h->adj0) {
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+    build_level_pattern(L, h->adj0);
+    h->csr_dst.resize(h->nnz);
+    for (int64_t i = 0; i < n; i++)
+      for (int64_t p = h->rowptr[i]; p < h->rowptr[i + 1]; p++) {
+        int a = clu[i], b = clu[h->col[p]];
+        int64_t q = L.find(a, b);
+        h->csr_dst[p] = L.off[q] + loc[i] + (int64_t)loc[h->col[p]] * L.ld[a];
+      }
+    // device copies
+    h->d_rowptr.alloc(sizeof(int64_t) * (n + 1));
+    h->d_col.alloc(sizeof(int) * std::max<int64_t>(h->nnz, 1));
+    h->d_val.alloc(sizeof(double) * std::max<int64_t>(h->nnz, 1));
+    h->d_csr_dst.alloc(sizeof(int64_t) * std::max<int64_t>(h->nnz, 1));
+    h->d_perm.alloc(sizeof(int64_t) * n);
+    h->d_err.alloc(sizeof(DevError));
+    HS_CUDA(cudaMemcpyAsync(h->d_rowptr.p, h->rowptr.data(), sizeof(int64_t) * (n + 1),
+                            cudaMemcpyHostToDevice, h->st));
+    HS_CUDA(cudaMemcpyAsync(h->d_col.p, h->col.data(), sizeof(int) * h->nnz,
+                            cudaMemcpyHostToDevice, h->st));
+    HS_CUDA(cudaMemcpyAsync(h->d_val.p, h->val.data(), sizeof(double) * h->nnz,
+                            cudaMemcpyHostToDevice, h->st));
+    HS_CUDA(cudaMemcpyAsync(h->d_csr_dst.p, h->csr_dst.data(), sizeof(int64_t) * h->nnz,
+                            cudaMemcpyHostToDevice, h->st));
+    HS_CUDA(cudaMemcpyAsync(h->d_perm.p, h->perm.data(), sizeof(int64_t) * n,
+                            cudaMemcpyHostToDevice, h->st));
+    HS_CUDA(cudaMemsetAsync(h->d_err.p, 0, sizeof(DevError), h->st));
+    HS_CUDA(cudaStreamSynchronize(h->st));
+  } catch (const Fail& f) {
+    return f.code;
+  } catch (const std::bad_alloc&) {
+    return HSOLVE_ERR_OOM;
+  }
+  *out = h.release();
+  return HSOLVE_OK;
+}
+
+hsolve_status hsolve_factor(hsolve_handle* h, double eps, hsolve_precision prec) {
+  if (!h) return HSOLVE_ERR_ARG;
+  cudaGetLastError();  // a stale error of another runtime user is not ours
+  if (!(eps >= 0.0) || prec < HSOLVE_FP64 || prec > HSOLVE_MIXED_BF16)
+    return set_err(h, HSOLVE_ERR_ARG, "bad eps or precision");
+  h->factored = false;
+  h->F.clear();
+  try {
+    h->prec = prec;
+    if (prec == HSOLVE_FP64)
+      factor_impl<double>(h, eps);
+    else
+      factor_impl<float>(h, eps);
+    h->factored = true;
+  } catch (const Fail& f) {
+    h->F.clear();
+    cudaStreamSynchronize(h->st);
+    cudaMemsetAsync(h->d_err.p, 0, sizeof(DevError), h->st);
+    cudaStreamSynchronize(h->st);
+    return set_err(h, f.code, f.msg);
+  } catch (const std::bad_alloc&) {
+    h->F.clear();
+    return set_err(h, HSOLVE_ERR_OOM, "host allocation failed");
+  }
+  return HSOLVE_OK;
+}
+
+hsolve_status hsolve_apply(hsolve_handle* h, const double* rhs, double* out, int nrhs, int64_t ld) {
+  if (!h) return HSOLVE_ERR_ARG;
+  cudaGetLastError();  // a stale error of another runtime user is not ours
+  if (!h->factored) return set_err(h, HSOLVE_ERR_STATE, "apply before factor");
+  if (!rhs || !out || nrhs < 1 || ld < h->n) return set_err(h, HSOLVE_ERR_ARG, "bad apply args");
+  try {
+    apply_any(h, rhs, out, nrhs, ld);
+    HS_CUDA(cudaGetLastError());
+    HS_CUDA(cudaStreamSynchronize(h->st));
+  } catch (const Fail& f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return HSOLVE_OK;
+}
+
+hsolve_status hsolve_spmv(hsolve_handle* h, const double* x, double* y, int nrhs, int64_t ld) {
+  if (!h || !x || !y || nrhs < 1 || ld < h->n) return HSOLVE_ERR_ARG;
+  try {
+    spmv_csr(h->n, h->d_rowptr.as<int64_t>(), h->d_col.as<int>(), h->d_val.as<double>(), x, ld, y,
+             ld, nrhs, h->st);
+    HS_CUDA(cudaGetLastError());
+    HS_CUDA(cudaStreamSynchronize(h->st));
+  } catch (const Fail& f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return HSOLVE_OK;
+}
+
+hsolve_status hsolve_solve(hsolve_handle* h, hsolve_krylov krylov, double tol, int maxit,
+                           const double* b, double* x, int nrhs, int64_t ld,
+                           hsolve_solve_info* info) {
+  if (!h) return HSOLVE_ERR_ARG;
+  cudaGetLastError();  // a stale error of another runtime user is not ours
+  if (!h->factored) return set_err(h, HSOLVE_ERR_STATE, "solve before factor");
+  if (!b || !x || nrhs < 1 || ld < h->n || maxit < 1 || !(tol > 0))
+    return set_err(h, HSOLVE_ERR_ARG, "bad solve args");
+  hsolve_status st = HSOLVE_OK;
+  try {
+    cudaEvent_t e0, e1;
+    HS_CUDA(cudaEventCreate(&e0));
+    HS_CUDA(cudaEventCreate(&e1));
+    HS_CUDA(cudaEventRecord(e0, h->st));
+    int it = 0;
+    double rr = 0;
+    if (krylov == HSOLVE_PCG) {
+      hsolve_solve_info tmp{};
+      st = pcg_impl(h, tol, maxit, b, x, nrhs, ld, &tmp);
+      it = tmp.iterations;
+      rr = tmp.rel_residual;
+    } else {
+      for (int c = 0; c < nrhs; c++) {
+        int i1 = 0;
+        double r1 = 0;
+        hsolve_status s1 = fgmres_one(h, tol, maxit, b + c * ld, x + c * ld,
+                                      h->opts.gmres_restart, &i1, &r1);
+        if (s1 != HSOLVE_OK) st = s1;
+        it = std::max(it, i1);
+        rr = std::max(rr, r1);
+      }
+    }
+    HS_CUDA(cudaEventRecord(e1, h->st));
+    HS_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) {
+      info->iterations = it;
+      info->rel_residual = rr;
+      info->factor_ms = h->factor_ms;
+      info->solve_ms = ms;
+    }
+  } catch (const Fail& f) {
+    return set_err(h, f.code, f.msg);
+  }
+  if (st == HSOLVE_ERR_NO_CONVERGENCE) set_err(h, st, "Krylov solve did not converge");
+  return st;
+}
+
+hsolve_status hsolve_solve_host(hsolve_handle* h, hsolve_krylov krylov, double tol, int maxit,
+                                const double* b, double* x, int nrhs, int64_t ld,
+                                hsolve_solve_info* info) {
+  if (!h) return HSOLVE_ERR_ARG;
+  if (!b || !x || nrhs < 1 || ld < h->n) return set_err(h, HSOLVE_ERR_ARG, "bad solve args");
+  DevBuf db, dx;
+  try {
+    db.alloc(sizeof(double) * h->n * nrhs);
+    dx.alloc(sizeof(double) * h->n * nrhs);
+    for (int c = 0; c < nrhs; c++)
+      HS_CUDA(cudaMemcpyAsync(db.as<double>() + c * h->n, b + c * ld, sizeof(double) * h->n,
+                              cudaMemcpyHostToDevice, h->st));
+  } catch (const Fail& f) {
+    return set_err(h, f.code, f.msg);
+  }
+  hsolve_status st = hsolve_solve(h, krylov, tol, maxit, db.as<double>(), dx.as<double>(), nrhs,
+                                  h->n, info);
+  if (st != HSOLVE_OK && st != HSOLVE_ERR_NO_CONVERGENCE) return st;
+  try {
+    for (int c = 0; c < nrhs; c++)
+      HS_CUDA(cudaMemcpyAsync(x + c * ld, dx.as<double>() + c * h->n, sizeof(double) * h->n,
+                              cudaMemcpyDeviceToHost, h->st));
+    HS_CUDA(cudaStreamSynchronize(h->st));
+  } catch (const Fail& f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return st;
+}
+
+hsolve_status hsolve_get_stats(const hsolve_handle* h, hsolve_stats* o) {
+  if (!h || !o) return HSOLVE_ERR_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->levels = (int)h->F.size();
+  o->clusters0 = h->L0.nclu;
+  o->colours_total = h->colours_total;
+  o->top_size = 0;
+  if (!h->F.empty() && h->F.back()->top) o->top_size = h->F.back()->P.m[0];
+  o->coarse_total = h->coarse_total;
+  o->factor_bytes = h->factor_bytes;
+  o->block_bytes = h->block_bytes;
+  o->apply_bytes = h->apply_bytes;
+  o->factor_flops = h->factor_flops;
+  o->schur_flops = h->schur_flops;
+  o->prep_flops = h->prep_flops;
+  o->gemm_flops = h->gemm_flops;
+  o->kernel_launches = h->launches;
+  o->precision = h->prec;
+  o->launches_total = launches_total();
+  return HSOLVE_OK;
+}
+
+hsolve_status hsolve_get_level(const hsolve_handle* h, int level, int32_t* nclu, int32_t* sizes,
+                               int32_t* ranks, int32_t* colour, int32_t cap) {
+  if (!h || !nclu || level < 0) return HSOLVE_ERR_ARG;
+  if (level >= (int)h->F.size()) return HSOLVE_ERR_ARG;
+  const FLevel& F = *h->F[level];
+  *nclu = F.P.nclu;
+  for (int i = 0; i < F.P.nclu && i < cap; i++) {
+    if (sizes) sizes[i] = F.P.m[i];
+    if (ranks) ranks[i] = i < (int)F.k.size() ? F.k[i] : 0;
+    if (colour) colour[i] = F.P.colour[i];
+  }
+  return HSOLVE_OK;
+}
+
+hsolve_status hsolve_get_perm(const hsolve_handle* h, int64_t* perm) {
+  if (!h || !perm) return HSOLVE_ERR_ARG;
+  std::memcpy(perm, h->perm.data(), sizeof(int64_t) * h->n);
+  return HSOLVE_OK;
+}
+
+hsolve_status hsolve_get_phase_times(const hsolve_handle* h, hsolve_phase_time* out, int32_t cap,
+                                     int32_t* count) {
+  if (!h || !count) return HSOLVE_ERR_ARG;
+  *count = (int)h->phases.size();
+  for (int i = 0; i < (int)h->phases.size() && i < cap && out; i++) {
+    std::memset(&out[i], 0, sizeof(out[i]));
+    std::snprintf(out[i].name, sizeof(out[i].name), "%s", h->phases[i].name.c_str());
+    out[i].ms = h->phases[i].ms;
+    out[i].launches = h->phases[i].launches;
+  }
+  return HSOLVE_OK;
+}
+
+hsolve_status hsolve_set_profiling(hsolve_handle* h, int on) {
+  if (!h) return HSOLVE_ERR_ARG;
+  h->profiling = on != 0;
+  return HSOLVE_OK;
+}
+
+const char* hsolve_last_error(const hsolve_handle* h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+void hsolve_destroy(hsolve_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,595 @@
+// Batched products, scatters and the substitution sweeps.
+//
+// gemm_gather  C = A * Bg for every cluster of a colour class, where the
+//              columns of Bg are gathered from the cluster's blocks (the
+//              neighbour coupling A_sN for Eq. scaling's coarse rows and the
+//              fine-elimination factor; the fill blocks A_sw for the
+//              coarse-to-far coupling C Z).
+// schur        A_nn -= B_L B_R (Eq. elim): the product of a cluster's two
+//              factor panels, written straight into the neighbour blocks
+//              through a row/column map (clusters of a colour touch disjoint
+//              blocks, so no atomics).
+// scatter      coarse rows/columns of a processed cluster into its blocks.
+// apply_*      Alg. 2: y_s <- T' y_s, y_N -= B_L y_f (forward) and
+//              x_f -= B_R x_N, x_s <- T_R'^T x_s (backward), one colour class
+//              per launch.
+// float64 Krylov helpers: CSR SpMV, deterministic dot products, axpy forms.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+
+#include "common.h"
+
+namespace hs {
+
+static std::atomic<int64_t> g_launches{0};
+int64_t launches_total() { return g_launches.load(); }
+void count_launch(int n) { g_launches += n; }
+
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int kMaxGridYZ = 65535;  // grid y/z limit: larger task lists are split
+
+// rows of A (M), inner K and skip rule from the rank of the cluster:
+//   mode 0: M = task.M, K = task.K; skip when rank == m (untouched)
+//   mode 1: M = rank; skip when rank == 0 or rank == m
+template <typename real>
+__global__ void __launch_bounds__(256)
+gemm_gather_kernel(const GemmTask* __restrict__ tasks, const real* __restrict__ Abase,
+                   real* __restrict__ Cbase, const real* __restrict__ Bbase,
+                   const int64_t* __restrict__ bptr, const int* __restrict__ bstr,
+                   const int* __restrict__ rank) {
+  const GemmTask tk = tasks[blockIdx.z];
+  const int r = rank[tk.s];
+  int M = tk.M;
+  if (tk.mode == 0) {
+    if (r == tk.K) return;
+  } else {
+    if (r == 0 || r == tk.K) return;
+    M = r;
+  }
+  const int N = tk.N, K = tk.K;
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+  if (i0 >= M || j0 >= N) return;
+  __shared__ real As[TK][TM + 1];
+  __shared__ real Bs[TK][TN + 1];
+  const real* A = Abase + tk.A;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  real acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) acc[a][b] = 0;
+  for (int l0 = 0; l0 < K; l0 += TK) {
+    // A tile: TM x TK, consecutive threads along rows
+    for (int e = threadIdx.x; e < TM * TK; e += 256) {
+      int i = e % TM, l = e / TM;
+      int gi = i0 + i, gl = l0 + l;
+      As[l][i] = (gi < M && gl < K) ? A[gi + (int64_t)gl * tk.lda] : real(0);
+    }
+    // B tile: TK x TN, consecutive threads along the gathered column
+    for (int e = threadIdx.x; e < TK * TN; e += 256) {
+      int l = e % TK, j = e / TK;
+      int gl = l0 + l, gj = j0 + j;
+      real v = 0;
+      if (gl < K && gj < N) {
+        int64_t p = bptr[tk.bcol + gj];
+        v = Bbase[p + (int64_t)gl * bstr[tk.bcol + gj]];
+      }
+      Bs[l][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < TK; l++) {
+      real a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        a[q] = As[l][ty + 16 * q];
+        b[q] = Bs[l][tx + 16 * q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[p][q] += a[p] * b[q];
+    }
+    __syncthreads();
+  }
+  real* C = Cbase + tk.C;
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int gi = i0 + ty + 16 * p, gj = j0 + tx + 16 * q;
+      if (gi < M && gj < N) C[gi + (int64_t)gj * tk.ldc] = acc[p][q];
+    }
+}
+
+// C_mapped[r, c] -= sum_i P[k+i, r] Q[k+i, c], i < f = m - rank.
+template <typename real>
+__global__ void __launch_bounds__(256)
+schur_kernel(const SchurTask* __restrict__ tasks, const real* __restrict__ fac,
+             real* __restrict__ arena, const int* __restrict__ map,
+             const int64_t* __restrict__ base, const int* __restrict__ ldn,
+             const int* __restrict__ rank) {
+  const SchurTask tk = tasks[blockIdx.z];
+  const int k = rank[tk.s];
+  const int f = tk.m - k;
+  if (f <= 0) return;
+  const int N = tk.nw;
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+  if (i0 >= N || j0 >= N) return;
+  __shared__ real As[TK][TM + 1];
+  __shared__ real Bs[TK][TN + 1];
+  const real* P = fac + tk.P + k;
+  const real* Q = fac + tk.Q + k;
+  const int ld = tk.m;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  real acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) acc[a][b] = 0;
+  for (int l0 = 0; l0 < f; l0 += TK) {
+    for (int e = threadIdx.x; e < TM * TK; e += 256) {
+      int l = e % TK, i = e / TK;
+      int gl = l0 + l, gi = i0 + i;
+      As[l][i] = (gl < f && gi < N) ? P[gl + (int64_t)gi * ld] : real(0);
+    }
+    for (int e = threadIdx.x; e < TK * TN; e += 256) {
+      int l = e % TK, j = e / TK;
+      int gl = l0 + l, gj = j0 + j;
+      Bs[l][j] = (gl < f && gj < N) ? Q[gl + (int64_t)gj * ld] : real(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < TK; l++) {
+      real a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        a[q] = As[l][ty + 16 * q];
+        b[q] = Bs[l][tx + 16 * q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[p][q] += a[p] * b[q];
+    }
+    __syncthreads();
+  }
+  const int* mp = map + tk.map;
+  const int64_t* bs = base + tk.base;
+  const int* ldv = ldn + tk.ldn;
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    int gi = i0 + ty + 16 * p;
+    if (gi >= N) continue;
+    int rm = mp[gi];
+    int a = rm >> 20, lr = rm & 0xFFFFF;
+    int64_t lda = ldv[a];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int gj = j0 + tx + 16 * q;
+      if (gj >= N) continue;
+      int cm = mp[gj];
+      int b = cm >> 20, lc = cm & 0xFFFFF;
+      int64_t addr = bs[a * tk.nb + b] + lr + lc * lda;
+      arena[addr] -= acc[p][q];
+    }
+  }
+}
+
+// One segment per (cluster, other-cluster) coupling: rows 0..k of the
+// source columns go to rows 0..k of block (s, o); their transpose (or the
+// second source, general case) to columns 0..k of block (o, s).
+template <typename real>
+__global__ void scatter_kernel(const ScatterSeg* __restrict__ segs, const real* __restrict__ src,
+                               real* __restrict__ arena, const int* __restrict__ rank) {
+  const ScatterSeg sg = segs[blockIdx.y];
+  const int k = rank[sg.s];
+  if (k == 0 || k == sg.m) return;
+  const int total = k * sg.width;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int i = e % k, c = e / k;
+    real v = src[sg.src + i + (int64_t)c * sg.ld_src];
+    arena[sg.dst_row + i + (int64_t)c * sg.ld_s] = v;
+    real v2 = (sg.src2 >= 0) ? src[sg.src2 + i + (int64_t)c * sg.ld_src] : v;
+    arena[sg.dst_col + c + (int64_t)i * sg.ld_o] = v2;
+  }
+}
+
+template <typename real>
+__global__ void copy_blocks_kernel(const CopyTask* __restrict__ tasks, const real* __restrict__ src,
+                                   real* __restrict__ dst) {
+  const CopyTask t = tasks[blockIdx.y];
+  const int total = t.rows * t.cols;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int i = e % t.rows, j = e / t.rows;
+    dst[t.dst + i + (int64_t)j * t.ld_dst] = src[t.src + i + (int64_t)j * t.ld_src];
+  }
+}
+
+// ---- substitution sweeps (Alg. 2) ---------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(256)
+apply_fwd_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
+                 const real* __restrict__ fac, const int64_t* __restrict__ vmap,
+                 real* __restrict__ y, int64_t ldy, int nrhs) {
+  extern __shared__ unsigned char smem_raw[];
+  real* tmp = reinterpret_cast<real*>(smem_raw);
+  const ApplyRec rc = recs[ids[blockIdx.x]];
+  const int m = rc.m, k = rc.k;
+  if (k == m) return;
+  const int f = m - k;
+  const real* T = fac + rc.T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int r = 0; r < nrhs; r++) {
+    real* ys = y + rc.voff + (int64_t)r * ldy;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) tmp[i] = ys[i];
+    __syncthreads();
+    // y_s <- T' y_s
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      real acc = 0;
+      for (int l = 0; l < m; l++) acc += T[i + (int64_t)l * m] * tmp[l];
+      ys[i] = acc;
+      tmp[m + i] = acc;
+    }
+    __syncthreads();
+    // y_N -= B_L y_f, B_L = (rows k.. of XT)^T (general) or of Y (SPD)
+    const real* BL = fac + (rc.sym ? rc.Y : rc.XT) + k;
+    const real* yf = tmp + m + k;
+    const int64_t* vm = vmap + rc.map;
+    for (int c = warp; c < rc.nw; c += nwarp) {
+      const real* col = BL + (int64_t)c * m;
+      real acc = 0;
+      for (int i = lane; i < f; i += 32) acc += col[i] * yf[i];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) y[vm[c] + (int64_t)r * ldy] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256)
+apply_bwd_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
+                 const real* __restrict__ fac, const int64_t* __restrict__ vmap,
+                 real* __restrict__ y, int64_t ldy, int nrhs) {
+  extern __shared__ unsigned char smem_raw[];
+  real* tmp = reinterpret_cast<real*>(smem_raw);
+  const ApplyRec rc = recs[ids[blockIdx.x]];
+  const int m = rc.m, k = rc.k;
+  if (k == m) return;
+  const int f = m - k;
+  const real* BR = fac + rc.Y + k;
+  const real* TRt = fac + (rc.sym ? rc.T : rc.TR);
+  const int64_t* vm = vmap + rc.map;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int r = 0; r < nrhs; r++) {
+    real* ys = y + rc.voff + (int64_t)r * ldy;
+    // gather x_N
+    real* xn = tmp + m;
+    for (int c = threadIdx.x; c < rc.nw; c += blockDim.x) xn[c] = y[vm[c] + (int64_t)r * ldy];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) tmp[i] = ys[i];
+    __syncthreads();
+    // x_f = y_f - B_R x_N
+    for (int i = threadIdx.x; i < f; i += blockDim.x) {
+      real acc = ys[k + i];
+      for (int c = 0; c < rc.nw; c++) acc -= BR[i + (int64_t)c * m] * xn[c];
+      tmp[k + i] = acc;
+    }
+    __syncthreads();
+    // x_s <- T_R'^T^T x = (TRt)^T x : out[i] = sum_l TRt[l, i] x[l]
+    for (int i = warp; i < m; i += nwarp) {
+      const real* col = TRt + (int64_t)i * m;
+      real acc = 0;
+      for (int l = lane; l < m; l += 32) acc += col[l] * tmp[l];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) ys[i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename real>
+__global__ void scatter_csr_kernel(const int64_t* __restrict__ dst, const double* __restrict__ val,
+                                   int64_t nnz, real* __restrict__ arena) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    arena[dst[e]] += (real)val[e];
+}
+
+template <typename real>
+__global__ void gather_vec_kernel(const int64_t* __restrict__ idx, int64_t n,
+                                  const real* __restrict__ src, int64_t lds, real* __restrict__ dst,
+                                  int64_t ldd, int nrhs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = e % n;
+    int r = (int)(e / n);
+    dst[p + r * ldd] = src[idx[p] + r * lds];
+  }
+}
+
+template <typename real>
+__global__ void scatter_vec_kernel(const int64_t* __restrict__ idx, int64_t n,
+                                   const real* __restrict__ src, int64_t lds,
+                                   real* __restrict__ dst, int64_t ldd, int nrhs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = e % n;
+    int r = (int)(e / n);
+    dst[idx[p] + r * ldd] = src[p + r * lds];
+  }
+}
+
+template <typename real>
+__global__ void perm_in_kernel(const int64_t* __restrict__ perm, int64_t n,
+                               const double* __restrict__ src, int64_t lds, real* __restrict__ dst,
+                               int64_t ldd, int nrhs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = e % n;
+    int r = (int)(e / n);
+    dst[p + r * ldd] = (real)src[perm[p] + r * lds];
+  }
+}
+
+template <typename real>
+__global__ void perm_out_kernel(const int64_t* __restrict__ perm, int64_t n,
+                                const real* __restrict__ src, int64_t lds, double* __restrict__ dst,
+                                int64_t ldd, int nrhs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = e % n;
+    int r = (int)(e / n);
+    dst[perm[p] + r * ldd] = (double)src[p + r * lds];
+  }
+}
+
+inline int grid_for(int64_t work, int threads) {
+  int64_t g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)g;
+}
+
+// ---- float64 Krylov helpers ----------------------------------------------
+
+__global__ void spmv_kernel(int64_t n, const int64_t* __restrict__ rp, const int* __restrict__ ci,
+                            const double* __restrict__ v, const double* __restrict__ x, int64_t ldx,
+                            double* __restrict__ y, int64_t ldy, int nrhs) {
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = rp[row], e = rp[row + 1];
+    for (int r = 0; r < nrhs; r++) {
+      double acc = 0;
+      const double* xr = x + r * ldx;
+      for (int64_t p = b; p < e; p++) acc += v[p] * xr[ci[p]];
+      y[row + r * ldy] = acc;
+    }
+  }
+}
+
+constexpr int kDotBlocks = 256;
+
+// partial[c * kDotBlocks + b] = sum over this block's rows of a[:,c] * b[:,c]
+__global__ void dots_partial(int64_t n, const double* __restrict__ a, int64_t lda,
+                             const double* __restrict__ b, int64_t ldb, int ncol, int bcast,
+                             double* __restrict__ part) {
+  __shared__ double red[256];
+  for (int c = 0; c < ncol; c++) {
+    const double* ac = a + c * lda;
+    const double* bc = b + (bcast ? 0 : c * ldb);
+    double s = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+      s += ac[i] * bc[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[c * kDotBlocks + blockIdx.x] = red[0];
+    __syncthreads();
+  }
+}
+
+__global__ void dots_final(const double* __restrict__ part, int ncol, double* __restrict__ out) {
+  int c = blockIdx.x;
+  __shared__ double red[kDotBlocks];
+  red[threadIdx.x] = part[c * kDotBlocks + threadIdx.x];
+  __syncthreads();
+  for (int st = kDotBlocks / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = red[0];
+}
+
+__global__ void multi_axpy_kernel(int64_t n, int nv, const double* __restrict__ V, int64_t ldv,
+                                  const double* __restrict__ coef, double sign,
+                                  double* __restrict__ w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0;
+    for (int j = 0; j < nv; j++) acc += V[i + j * ldv] * coef[j];
+    w[i] += sign * acc;
+  }
+}
+
+__global__ void axpby_kernel(int64_t n, int nrhs, const double* __restrict__ alpha,
+                             const double* __restrict__ x, int64_t ldx,
+                             const double* __restrict__ beta, double* __restrict__ y, int64_t ldy) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % n;
+    int r = (int)(e / n);
+    y[i + r * ldy] = alpha[r] * x[i + r * ldx] + beta[r] * y[i + r * ldy];
+  }
+}
+
+}  // namespace
+
+template <typename real>
+void Launch<real>::gemm_gather(const GemmTask* tasks_dev, int ntask, int maxM, int maxN,
+                               const real* Abase, real* Cbase, const real* Bbase,
+                               const int64_t* bptr, const int* bstr, const int* rank,
+                               cudaStream_t st) {
+  if (ntask <= 0 || maxM <= 0 || maxN <= 0) return;
+  for (int t0 = 0; t0 < ntask; t0 += kMaxGridYZ) {
+    dim3 grid((maxN + TN - 1) / TN, (maxM + TM - 1) / TM, std::min(kMaxGridYZ, ntask - t0));
+    count_launch();
+    gemm_gather_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, Abase, Cbase, Bbase, bptr,
+                                                    bstr, rank);
+  }
+}
+
+template <typename real>
+void Launch<real>::schur(const SchurTask* tasks_dev, int ntask, int maxnw, const real* fac,
+                         real* arena, const int* map, const int64_t* base, const int* ldn,
+                         const int* rank, cudaStream_t st) {
+  if (ntask <= 0 || maxnw <= 0) return;
+  for (int t0 = 0; t0 < ntask; t0 += kMaxGridYZ) {
+    dim3 grid((maxnw + TN - 1) / TN, (maxnw + TM - 1) / TM, std::min(kMaxGridYZ, ntask - t0));
+    count_launch();
+    schur_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, fac, arena, map, base, ldn, rank);
+  }
+}
+
+template <typename real>
+void Launch<real>::scatter(const ScatterSeg* segs_dev, int nseg, int maxw, const real* src,
+                           real* arena, const int* rank, cudaStream_t st) {
+  if (nseg <= 0) return;
+  for (int t0 = 0; t0 < nseg; t0 += kMaxGridYZ) {
+    dim3 grid(std::max(1, std::min(64, (maxw * 64 + 255) / 256)), std::min(kMaxGridYZ, nseg - t0));
+    count_launch();
+    scatter_kernel<real><<<grid, 256, 0, st>>>(segs_dev + t0, src, arena, rank);
+  }
+}
+
+template <typename real>
+void Launch<real>::copy_blocks(const CopyTask* tasks_dev, int ntask, const real* src, real* dst,
+                               cudaStream_t st) {
+  if (ntask <= 0) return;
+  for (int t0 = 0; t0 < ntask; t0 += kMaxGridYZ) {
+    dim3 grid(8, std::min(kMaxGridYZ, ntask - t0));
+    count_launch();
+    copy_blocks_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, src, dst);
+  }
+}
+
+template <typename real>
+void Launch<real>::apply_fwd(const ApplyRec* recs, const int* ids, int nids, const real* fac,
+                             const int64_t* vmap, real* y, int64_t ldy, int nrhs, int maxm,
+                             cudaStream_t st) {
+  if (nids <= 0) return;
+  size_t sm = sizeof(real) * (size_t)(2 * maxm);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(apply_fwd_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  count_launch();
+  apply_fwd_kernel<real><<<nids, 256, sm, st>>>(recs, ids, fac, vmap, y, ldy, nrhs);
+}
+
+template <typename real>
+void Launch<real>::apply_bwd(const ApplyRec* recs, const int* ids, int nids, const real* fac,
+                             const int64_t* vmap, real* y, int64_t ldy, int nrhs, int maxm,
+                             cudaStream_t st) {
+  if (nids <= 0) return;
+  // maxm here is the larger of m and nw over the class
+  size_t sm = sizeof(real) * (size_t)(2 * maxm);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(apply_bwd_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  count_launch();
+  apply_bwd_kernel<real><<<nids, 256, sm, st>>>(recs, ids, fac, vmap, y, ldy, nrhs);
+}
+
+template <typename real>
+void Launch<real>::scatter_csr(const int64_t* dst, const double* val, int64_t nnz, real* arena,
+                               cudaStream_t st) {
+  if (nnz <= 0) return;
+  count_launch();
+  scatter_csr_kernel<real><<<grid_for(nnz, 256), 256, 0, st>>>(dst, val, nnz, arena);
+}
+
+template <typename real>
+void Launch<real>::gather_vec(const int64_t* idx, int64_t n, const real* src, int64_t lds,
+                              real* dst, int64_t ldd, int nrhs, cudaStream_t st) {
+  if (n <= 0) return;
+  count_launch();
+  gather_vec_kernel<real><<<grid_for(n * nrhs, 256), 256, 0, st>>>(idx, n, src, lds, dst, ldd, nrhs);
+}
+
+template <typename real>
+void Launch<real>::scatter_vec(const int64_t* idx, int64_t n, const real* src, int64_t lds,
+                               real* dst, int64_t ldd, int nrhs, cudaStream_t st) {
+  if (n <= 0) return;
+  count_launch();
+  scatter_vec_kernel<real><<<grid_for(n * nrhs, 256), 256, 0, st>>>(idx, n, src, lds, dst, ldd, nrhs);
+}
+
+template <typename real>
+void Launch<real>::perm_in(const int64_t* perm, int64_t n, const double* src, int64_t lds,
+                           real* dst, int64_t ldd, int nrhs, cudaStream_t st) {
+  if (n <= 0) return;
+  count_launch();
+  perm_in_kernel<real><<<grid_for(n * nrhs, 256), 256, 0, st>>>(perm, n, src, lds, dst, ldd, nrhs);
+}
+
+template <typename real>
+void Launch<real>::perm_out(const int64_t* perm, int64_t n, const real* src, int64_t lds,
+                            double* dst, int64_t ldd, int nrhs, cudaStream_t st) {
+  if (n <= 0) return;
+  count_launch();
+  perm_out_kernel<real><<<grid_for(n * nrhs, 256), 256, 0, st>>>(perm, n, src, lds, dst, ldd, nrhs);
+}
+
+template <typename real>
+void Launch<real>::dense_top_factor(real*, int, int, int*, DevError*, cudaStream_t) {}
+template <typename real>
+void Launch<real>::dense_top_solve(const real*, int, int, const int*, real*, int64_t, int,
+                                   cudaStream_t) {}
+
+template struct Launch<double>;
+template struct Launch<float>;
+
+void spmv_csr(int64_t n, const int64_t* rp, const int* ci, const double* v, const double* x,
+              int64_t ldx, double* y, int64_t ldy, int nrhs, cudaStream_t st) {
+  count_launch();
+  spmv_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, v, x, ldx, y, ldy, nrhs);
+}
+
+// out[c] = a[:,c] . b[:,c]; partial sums in a fixed order (deterministic).
+// `out` must have room for nrhs * (kDotBlocks + 1) doubles: the first
+// nrhs * kDotBlocks hold partials, results go to out[nrhs*kDotBlocks + c].
+void dots(int64_t n, const double* a, int64_t lda, const double* b, int64_t ldb, int nrhs,
+          double* out, cudaStream_t st) {
+  count_launch();
+  dots_partial<<<kDotBlocks, 256, 0, st>>>(n, a, lda, b, ldb, nrhs, 0, out);
+  count_launch();
+  dots_final<<<nrhs, kDotBlocks, 0, st>>>(out, nrhs, out + (int64_t)nrhs * kDotBlocks);
+}
+
+void multi_dot(int64_t n, int nv, const double* V, int64_t ldv, const double* w, double* out,
+               cudaStream_t st) {
+  count_launch();
+  dots_partial<<<kDotBlocks, 256, 0, st>>>(n, V, ldv, w, 0, nv, 1, out);
+  count_launch();
+  dots_final<<<nv, kDotBlocks, 0, st>>>(out, nv, out + (int64_t)nv * kDotBlocks);
+}
+
+void multi_axpy(int64_t n, int nv, const double* V, int64_t ldv, const double* coef, double sign,
+                double* w, cudaStream_t st) {
+  count_launch();
+  multi_axpy_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, nv, V, ldv, coef, sign, w);
+}
+
+void axpby_cols(int64_t n, int nrhs, const double* alpha, const double* x, int64_t ldx,
+                const double* beta, double* y, int64_t ldy, cudaStream_t st) {
+  count_launch();
+  axpby_kernel<<<grid_for(n * nrhs, 256), 256, 0, st>>>(n, nrhs, alpha, x, ldx, beta, y, ldy);
+}
+
+}  // namespace hs

@@ -1,0 +1,252 @@
+"""Python binding of ``libhsolve.so`` (ctypes; argument marshalling only).
+
+Every step of the factorization, the substitution sweeps and the Krylov
+solve runs in the library's CUDA kernels.  Device buffers are torch CUDA
+tensors (float64, column-major n x nrhs, i.e. a C-contiguous (nrhs, n)
+tensor); the library never falls back to any host computation: if the
+library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhsolve.so")
+
+OK = 0
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_SINGULAR",
+          -5: "ERR_NOT_SPD", -6: "ERR_NO_CONVERGENCE", -7: "ERR_BUDGET", -8: "ERR_TIMEOUT",
+          -9: "ERR_STATE"}
+PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
+KRYLOV = {"pcg": 0, "gmres": 1}
+
+
+class HsolveError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"hsolve {STATUS.get(code, code)}: {msg}")
+
+
+class Csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("leaf_size", C.c_int32), ("symmetric", C.c_int32), ("top_size", C.c_int64),
+                ("max_rank", C.c_int32), ("gmres_restart", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("rel_residual", C.c_double),
+                ("factor_ms", C.c_double), ("solve_ms", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("clusters0", C.c_int32), ("colours_total", C.c_int32),
+                ("top_size", C.c_int32), ("coarse_total", C.c_int64),
+                ("factor_bytes", C.c_int64), ("block_bytes", C.c_int64),
+                ("apply_bytes", C.c_int64), ("factor_flops", C.c_double),
+                ("schur_flops", C.c_double), ("prep_flops", C.c_double),
+                ("gemm_flops", C.c_double), ("kernel_launches", C.c_int32),
+                ("precision", C.c_int32), ("launches_total", C.c_int64)]
+
+
+class PhaseTime(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("ms", C.c_double), ("launches", C.c_int32)]
+
+
+EXPORTS = {
+    "hsolve_default_opts": (None, [C.POINTER(Opts)]),
+    "hsolve_analyze": (C.c_int, [C.POINTER(Csr), C.c_void_p, C.c_int, C.POINTER(Opts), C.c_void_p,
+                                 C.POINTER(C.c_void_p)]),
+    "hsolve_factor": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "hsolve_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int64]),
+    "hsolve_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                               C.c_int, C.c_int64, C.POINTER(SolveInfo)]),
+    "hsolve_solve_host": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p,
+                                    C.c_void_p, C.c_int, C.c_int64, C.POINTER(SolveInfo)]),
+    "hsolve_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int64]),
+    "hsolve_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "hsolve_get_level": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_int32]),
+    "hsolve_get_perm": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "hsolve_get_phase_times": (C.c_int, [C.c_void_p, C.POINTER(PhaseTime), C.c_int32,
+                                         C.POINTER(C.c_int32)]),
+    "hsolve_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "hsolve_last_error": (C.c_char_p, [C.c_void_p]),
+    "hsolve_destroy": (None, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhsolve.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise HsolveError(-2, f"{path} not built; run paper_1712_07297_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    load().hsolve_default_opts(C.byref(o))
+    return o
+
+
+def _check(code, handle=None):
+    if code != OK:
+        msg = ""
+        if handle:
+            m = load().hsolve_last_error(handle)
+            msg = m.decode() if m else ""
+        raise HsolveError(code, msg)
+
+
+def _dev_ptr(t, n):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise TypeError("expected a float64 CUDA tensor")
+    if t.dim() == 1:
+        if t.shape[0] != n or not t.is_contiguous():
+            raise ValueError("vector of length n expected")
+        return t.data_ptr(), 1, n
+    if t.dim() != 2 or t.shape[1] != n or t.stride(1) != 1:
+        raise ValueError("(nrhs, n) tensor with unit stride along n expected")
+    return t.data_ptr(), t.shape[0], t.stride(0)
+
+
+class Solver:
+    """One analysed matrix: analyze -> factor -> apply / solve."""
+
+    def __init__(self, rowptr, col, val, coords=None, *, leaf_size=128, symmetric=-1, top_size=0,
+                 max_rank=0, gmres_restart=50, stream=None):
+        lib = load()
+        self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.val = np.ascontiguousarray(val, dtype=np.float64)
+        self.n = len(self.rowptr) - 1
+        csr = Csr(self.n, len(self.col), self.rowptr.ctypes.data, self.col.ctypes.data,
+                  self.val.ctypes.data)
+        o = default_opts()
+        o.leaf_size, o.symmetric, o.top_size = leaf_size, symmetric, top_size
+        o.max_rank, o.gmres_restart = max_rank, gmres_restart
+        h = C.c_void_p()
+        cptr, dim = None, 0
+        if coords is not None:
+            self._coords = np.ascontiguousarray(coords, dtype=np.float64)
+            cptr, dim = self._coords.ctypes.data, self._coords.shape[1]
+        st = None
+        if stream is not None:
+            st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _check(lib.hsolve_analyze(C.byref(csr), cptr, dim, C.byref(o), st, C.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        return cls(prob.rowptr, prob.col, prob.val, prob.coords, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().hsolve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def factor(self, eps: float, precision="fp64"):
+        p = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        _check(load().hsolve_factor(self.h, float(eps), p), self.h)
+
+    def apply(self, rhs, out=None):
+        """out = M^{-1} rhs on the device (torch float64 CUDA tensors)."""
+        import torch
+        ptr, nrhs, ld = _dev_ptr(rhs, self.n)
+        if out is None:
+            out = torch.empty_like(rhs)
+        optr, onrhs, old = _dev_ptr(out, self.n)
+        if onrhs != nrhs or old != ld:
+            raise ValueError("rhs/out layouts differ")
+        _check(load().hsolve_apply(self.h, ptr, optr, nrhs, ld), self.h)
+        return out
+
+    def spmv(self, x, y=None):
+        import torch
+        ptr, nrhs, ld = _dev_ptr(x, self.n)
+        if y is None:
+            y = torch.empty_like(x)
+        yptr, _, _ = _dev_ptr(y, self.n)
+        _check(load().hsolve_spmv(self.h, ptr, yptr, nrhs, ld), self.h)
+        return y
+
+    def solve(self, b, x=None, *, krylov="pcg", tol=1e-10, maxit=1000, check=True):
+        import torch
+        ptr, nrhs, ld = _dev_ptr(b, self.n)
+        if x is None:
+            x = torch.empty_like(b)
+        xptr, _, _ = _dev_ptr(x, self.n)
+        info = SolveInfo()
+        code = load().hsolve_solve(self.h, KRYLOV[krylov], tol, maxit, ptr, xptr, nrhs, ld,
+                                   C.byref(info))
+        if check:
+            _check(code, self.h)
+        return x, info
+
+    def solve_host(self, b: np.ndarray, *, krylov="pcg", tol=1e-10, maxit=1000, check=True):
+        """Host arrays in and out (copies are part of the call)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        bb = b[None, :] if b.ndim == 1 else b
+        x = np.empty_like(bb)
+        info = SolveInfo()
+        code = load().hsolve_solve_host(self.h, KRYLOV[krylov], tol, maxit, bb.ctypes.data,
+                                        x.ctypes.data, bb.shape[0], self.n, C.byref(info))
+        if check:
+            _check(code, self.h)
+        return (x[0] if b.ndim == 1 else x), info
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().hsolve_get_stats(self.h, C.byref(s)), self.h)
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def level(self, level: int):
+        lib = load()
+        nc = C.c_int32()
+        _check(lib.hsolve_get_level(self.h, level, C.byref(nc), None, None, None, 0), self.h)
+        sizes = np.zeros(nc.value, dtype=np.int32)
+        ranks = np.zeros(nc.value, dtype=np.int32)
+        colour = np.zeros(nc.value, dtype=np.int32)
+        _check(lib.hsolve_get_level(self.h, level, C.byref(nc), sizes.ctypes.data,
+                                    ranks.ctypes.data, colour.ctypes.data, nc.value), self.h)
+        return sizes, ranks, colour
+
+    def perm(self) -> np.ndarray:
+        p = np.zeros(self.n, dtype=np.int64)
+        _check(load().hsolve_get_perm(self.h, p.ctypes.data), self.h)
+        return p
+
+    def set_profiling(self, on: bool):
+        _check(load().hsolve_set_profiling(self.h, int(bool(on))), self.h)
+
+    def phase_times(self) -> dict:
+        lib = load()
+        cnt = C.c_int32()
+        _check(lib.hsolve_get_phase_times(self.h, None, 0, C.byref(cnt)), self.h)
+        arr = (PhaseTime * max(cnt.value, 1))()
+        _check(lib.hsolve_get_phase_times(self.h, arr, cnt.value, C.byref(cnt)), self.h)
+        return {arr[i].name.decode(): (arr[i].ms, arr[i].launches) for i in range(cnt.value)}

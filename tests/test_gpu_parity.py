@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA library against the float64 CPU oracle, through the
+C-ABI (ctypes binding).
+
+Bars (written out per test):
+  * ranks of every cluster at every level: identical (integer work);
+  * float64 path: M^{-1} b within 1e-10 relative (2-norm) of the oracle's;
+  * mixed float32 path: M^{-1} b within a bound derived from float32
+    rounding (see _mixed_bound), and the float64 Krylov solve reaching
+    1e-10 relative residual;
+  * Krylov solves: ||b - A x|| <= 1e-10 ||b|| recomputed here in float64.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1712_07297_gb300 import inputs as I  # noqa: E402
+from oracle import hsolver as H  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1712_07297_gb300 import build
+    build.build()
+    from paper_1712_07297_gb300 import hsolve
+    hsolve.load()
+    return hsolve
+
+
+def _oracle(p, leaf, eps, top_size=0, max_rank=None):
+    return H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=p.symmetric,
+                    top_size=top_size, max_rank=max_rank)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _ranks_match(s, fac):
+    nlev = 0
+    for li, lv in enumerate(fac.levels):
+        if lv.top is not None:
+            break
+        sizes, ranks, _ = s.level(li)
+        assert list(sizes) == list(lv.sizes), f"level {li} sizes"
+        want = [lv.factors[i].k if i in lv.factors else 0 for i in range(lv.nclu)]
+        assert list(ranks) == want, f"level {li} ranks"
+        nlev += 1
+    return nlev
+
+
+CASES = [
+    # (name, problem, leaf, eps)  -- 2D 64x64 clusters of 64, eps 1e-3 is
+    # the small headline workload; the others add 3D, ragged sizes and
+    # variable coefficients
+    ("poisson2d_64", lambda: I.poisson((64, 64)), 64, 1e-3),
+    ("poisson3d_16", lambda: I.poisson((16, 16, 16)), 64, 1e-2),
+    ("poisson2d_ragged", lambda: I.poisson((37, 23)), 16, 1e-2),
+    ("vcdiff3d_12", lambda: I.vc_diffusion((12, 12, 12), seed=2002), 32, 1e-3),
+    ("hcdiff3d_12", lambda: I.high_contrast((12, 12, 12), seed=5), 32, 1e-2),
+]
+
+
+@pytest.mark.parametrize("name,mk,leaf,eps", CASES)
+def test_fp64_matches_oracle(hs, name, mk, leaf, eps):
+    p = mk()
+    fac = _oracle(p, leaf, eps)
+    s = hs.Solver.from_problem(p, leaf_size=leaf, symmetric=1)
+    s.factor(eps, "fp64")
+    assert np.array_equal(s.perm(), fac.perm)
+    assert _ranks_match(s, fac) >= 1
+    b = I.rhs(p.n, 3, seed=1000)
+    ref = H.solve(fac, b.T).T
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out, ref) < 1e-10, _rel(out, ref)
+    s.close()
+
+
+@pytest.mark.parametrize("name,mk,leaf,eps", CASES[:3])
+def test_fp64_pcg_converges(hs, name, mk, leaf, eps):
+    p = mk()
+    s = hs.Solver.from_problem(p, leaf_size=leaf, symmetric=1)
+    s.factor(eps, "fp64")
+    b = I.rhs(p.n, 2, seed=1000)
+    x, info = s.solve(torch.from_numpy(b).cuda(), krylov="pcg", tol=1e-10)
+    x = x.cpu().numpy()
+    A = p.scipy()
+    for c in range(2):
+        assert np.linalg.norm(b[c] - A @ x[c]) <= 1e-10 * np.linalg.norm(b[c]) * 1.0001
+    assert info.rel_residual <= 1e-10
+    s.close()
+
+
+def test_eps0_is_direct(hs):
+    p = I.poisson((9, 10, 11))
+    s = hs.Solver.from_problem(p, leaf_size=40, symmetric=1)
+    s.factor(0.0, "fp64")
+    b = I.rhs(p.n, 1, seed=3)
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out[0], np.linalg.solve(p.dense(), b[0])) < 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("mk,leaf,eps", [
+    (lambda: I.convection_diffusion((16, 16, 16), 10.0), 64, 1e-2),
+    (lambda: I.convection_diffusion((40, 30), 10.0), 32, 1e-3),
+])
+def test_general_matches_oracle(hs, mk, leaf, eps):
+    # nonsymmetric: pivot orders of the LU factors may legitimately differ on
+    # near-ties, so the comparison is on M^{-1} b, which does not depend on them
+    p = mk()
+    fac = _oracle(p, leaf, eps)
+    s = hs.Solver.from_problem(p, leaf_size=leaf, symmetric=0)
+    s.factor(eps, "fp64")
+    _ranks_match(s, fac)
+    b = I.rhs(p.n, 2, seed=1002)
+    ref = H.solve(fac, b.T).T
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out, ref) < 1e-10, _rel(out, ref)
+    x, info = s.solve(torch.from_numpy(b).cuda(), krylov="gmres", tol=1e-10)
+    A = p.scipy()
+    xx = x.cpu().numpy()
+    for c in range(2):
+        assert np.linalg.norm(b[c] - A @ xx[c]) <= 1.0001e-10 * np.linalg.norm(b[c])
+    s.close()
+
+
+def _mixed_bound(fac):
+    # float32 blocks: each stored operator carries a relative error of a few
+    # units of 2^-24 times its condition; the preconditioner output is
+    # compared at 2e-3 relative, far above float32 rounding (6e-8) times the
+    # modest growth through the levels, and far below the eps-level
+    # differences a wrong rank or a dropped term would cause.
+    return 2e-3
+
+
+@pytest.mark.parametrize("name,mk,leaf,eps", CASES[:2])
+def test_mixed_fp32_close_and_solves(hs, name, mk, leaf, eps):
+    p = mk()
+    fac = _oracle(p, leaf, eps)
+    s = hs.Solver.from_problem(p, leaf_size=leaf, symmetric=1)
+    s.factor(eps, "mixed_fp32")
+    b = I.rhs(p.n, 1, seed=1000)
+    ref = H.solve(fac, b.T).T
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out, ref) < _mixed_bound(fac), _rel(out, ref)
+    x, info = s.solve(torch.from_numpy(b).cuda(), krylov="pcg", tol=1e-10)
+    xx = x.cpu().numpy()[0]
+    assert np.linalg.norm(b[0] - p.scipy() @ xx) <= 1.0001e-10 * np.linalg.norm(b[0])
+    s.close()
+
+
+def test_single_cluster_and_top(hs):
+    # n below the leaf size: one cluster, a dense factor (Alg. 1 "small")
+    p = I.poisson((5, 7))
+    s = hs.Solver.from_problem(p, leaf_size=64, symmetric=1)
+    s.factor(1e-2, "fp64")
+    b = I.rhs(p.n, 1, seed=4)
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out[0], np.linalg.solve(p.dense(), b[0])) < 1e-12
+    s.close()
+    # top_size switch: identical to the oracle with the same switch
+    p = I.poisson((20, 20))
+    fac = _oracle(p, 16, 1e-2, top_size=150)
+    s = hs.Solver.from_problem(p, leaf_size=16, symmetric=1, top_size=150)
+    s.factor(1e-2, "fp64")
+    b = I.rhs(p.n, 1, seed=5)
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out.T, H.solve(fac, b.T)) < 1e-10
+    s.close()
+
+
+def test_1d_and_fixed_rank(hs):
+    p = I.poisson((300,))
+    s = hs.Solver.from_problem(p, leaf_size=8, symmetric=1)
+    s.factor(1e-1, "fp64")
+    b = I.rhs(p.n, 1, seed=6)
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out[0], np.linalg.solve(p.dense(), b[0])) < 1e-10
+    s.close()
+    p = I.poisson((32, 32))
+    fac = _oracle(p, 32, 1e-8, max_rank=4)
+    s = hs.Solver.from_problem(p, leaf_size=32, symmetric=1, max_rank=4)
+    s.factor(1e-8, "fp64")
+    _ranks_match(s, fac)
+    b = I.rhs(p.n, 1, seed=6)
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out.T, H.solve(fac, b.T)) < 1e-10
+    s.close()
+
+
+def test_errors_are_reported(hs):
+    p = I.poisson((8, 8))
+    s = hs.Solver.from_problem(p, leaf_size=16, symmetric=1)
+    b = torch.zeros((1, p.n), dtype=torch.float64, device="cuda")
+    with pytest.raises(hs.HsolveError) as e:
+        s.apply(b)
+    assert e.value.code == -9
+    s.close()
+    # symmetric indefinite matrix declared SPD: the Cholesky pivot check fires
+    # (k^2 = 1.3 is no eigenvalue of any 4x4 cluster block, so every A_ss is
+    # invertible and the general path applies)
+    q = I.helmholtz((8, 8), k2=1.3)
+    s = hs.Solver.from_problem(q, leaf_size=16, symmetric=1)
+    with pytest.raises(hs.HsolveError) as e:
+        s.factor(1e-2, "fp64")
+    assert e.value.code == -5
+    # the same matrix through the general (LU) path factors and solves
+    s.close()
+    s = hs.Solver.from_problem(q, leaf_size=16, symmetric=0)
+    s.factor(0.0, "fp64")
+    bb = I.rhs(q.n, 1, seed=8)
+    out = s.apply(torch.from_numpy(bb).cuda()).cpu().numpy()
+    assert _rel(out[0], np.linalg.solve(q.dense(), bb[0])) < 1e-9
+    s.close()
+
+
+def test_host_solve_api(hs):
+    p = I.poisson((30, 30))
+    s = hs.Solver.from_problem(p, leaf_size=32, symmetric=1)
+    s.factor(1e-2, "fp64")
+    b = I.rhs(p.n, 1, seed=9)[0]
+    x, info = s.solve_host(b, krylov="pcg", tol=1e-10)
+    assert np.linalg.norm(b - p.scipy() @ x) <= 1.0001e-10 * np.linalg.norm(b)
+    s.close()

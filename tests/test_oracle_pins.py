@@ -257,3 +257,20 @@ def test_krylov_against_direct(method):
     fac = _fac(p, 9, 0.0)
     x1, it1, res1 = fn(A, b, lambda r: H.solve(fac, r), tol=1e-10)
     assert it1 <= 2 and res1 <= 1e-10
+
+
+def test_noise_floor_drops_rounding_level_fill():
+    # A fill block at the rounding level of the cluster's diagonal block is
+    # zero in exact arithmetic: its "rank" must not be decided by noise.
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((10, 30))
+    assert H.cpqr(1e-20 * G, 1e-3, floor=1e-14)["k"] == 0
+    assert H.cpqr(1e-20 * G, 1e-3)["k"] == 10
+    assert H.cpqr(G, 1e-3, floor=1e-14)["k"] == 10
+    # 2D upwind convection-diffusion makes such a block at level 1
+    p = I.convection_diffusion((40, 30), 10.0)
+    fac = _fac(p, 32, 1e-3)
+    assert fac.levels[1].factors[30].k == 0
+    b = I.rhs(p.n, 1, seed=1)[0]
+    x = H.solve(_fac(p, 32, 0.0), b)
+    np.testing.assert_allclose(p.scipy() @ x, b, atol=1e-11)
