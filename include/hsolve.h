@@ -190,7 +190,8 @@ hsolve_status hsolve_get_phase_times(const hsolve_handle* h,
                                      int32_t* count);
 
 /* Enable (1) or disable (0) per-phase CUDA-event timing (off by default; it
- * adds a synchronisation per phase). */
+ * adds a synchronisation per phase); 2 also splits every phase by level
+ * (names "<phase>.L<level>"). */
 hsolve_status hsolve_set_profiling(hsolve_handle* h, int on);
 
 /* Text of the last error on this handle (never NULL). */

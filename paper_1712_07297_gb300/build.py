@@ -22,7 +22,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
 
-SOURCES = ["analyze.cpp", "hsolve.cu", "kernels_dense.cu", "kernels_misc.cu", "kernels_tc.cu"]
+SOURCES = ["analyze.cpp", "hsolve.cu", "kernels_dense.cu", "kernels_misc.cu", "kernels_apply.cu",
+           "kernels_tc.cu"]
 
 
 def _nvcc() -> str:

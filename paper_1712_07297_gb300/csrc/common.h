@@ -125,6 +125,7 @@ struct ApplyRec {   // one cluster's factor, as the substitution sweeps use it
   int64_t T, TR;    // T' (and T'_R) offsets in the factor arena
   int64_t Y, XT;    // B_R storage (rows k..m of Y) and B_L^T storage (XT)
   int64_t map;      // offset into the vector-index map (nw entries)
+  int64_t part;     // offset of the backward partial sums (per right-hand side)
 };
 
 template <typename real>
@@ -132,7 +133,7 @@ struct Launch {
   static void prep(const PrepTask* tasks_dev, int ntask, real* arena, real* fac,
                    real* ws, double* wsd, const int64_t* gptr, const int* gstr,
                    int* rank, double eps, int sym, int max_rank, int maxm,
-                   DevError* err, int level, cudaStream_t st);
+                   DevError* err, int level, long long* dbg, cudaStream_t st);
   static void gemm_gather(const GemmTask* tasks_dev, int ntask, int maxM, int maxN,
                           const real* Abase, real* Cbase, const real* Bbase,
                           const int64_t* bptr, const int* bstr, const int* rank,
@@ -144,12 +145,12 @@ struct Launch {
                       real* arena, const int* rank, cudaStream_t st);
   static void copy_blocks(const CopyTask* tasks_dev, int ntask, const real* src, real* dst,
                           cudaStream_t st);
-  static void apply_fwd(const ApplyRec* recs, const int* ids, int nids, const real* fac,
-                        const int64_t* vmap, real* y, int64_t ldy, int nrhs, int maxm,
-                        cudaStream_t st);
-  static void apply_bwd(const ApplyRec* recs, const int* ids, int nids, const real* fac,
-                        const int64_t* vmap, real* y, int64_t ldy, int nrhs, int maxm,
-                        cudaStream_t st);
+  static void apply_fwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int maxnw,
+                        const real* fac, const int64_t* vmap, real* y, real* z, int64_t ldy,
+                        int nrhs, cudaStream_t st);
+  static void apply_bwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int maxnw,
+                        const real* fac, const int64_t* vmap, real* y, real* z, real* part,
+                        int64_t ldy, int nrhs, cudaStream_t st);
   static void scatter_csr(const int64_t* dst, const double* val, int64_t nnz, real* arena,
                           cudaStream_t st);
   static void gather_vec(const int64_t* idx, int64_t n, const real* src, int64_t lds,

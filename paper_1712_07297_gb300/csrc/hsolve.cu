@@ -136,11 +136,13 @@ struct FLevel {
   DevBuf vmap;                        // int64 vector index maps
   DevBuf ids;                         // int cluster ids, class by class
   std::vector<int> cls_off;           // offsets of each class in ids
-  std::vector<int> cls_maxm;          // apply smem bound per class
+  std::vector<int> cls_maxm;          // largest m per class
+  std::vector<int> cls_maxnw;         // largest neighbour width per class
+  int64_t part_elems = 0;             // backward partial sums per right-hand side
   DevBuf next_idx;                    // int64 gather map to the next level
   int64_t next_n = 0;
-  DevBuf vec;                         // level vector buffer (real)
-  size_t vec_bytes = 0;
+  DevBuf vec, zvec, part;             // level vector, scratch vector, partial sums
+  int vec_nrhs = 0;
   bool top = false;
 };
 
@@ -176,9 +178,11 @@ struct hsolve_handle {
   DevBuf ws, wsd, blob_dev;
   PinnedBuf pin;
   DevBuf kry;  // Krylov vectors
+  DevBuf dbg;  // per-phase clock stamps of the prep kernel (profiling)
   DevBuf dots;
   PinnedBuf pin_small;
   bool profiling = false;
+  bool profile_levels = false;
   std::vector<PhaseTimer> phases;
   std::string err;
 };
@@ -232,6 +236,21 @@ struct EventPair {
 
 // Per-phase timing helper: records an event pair around a lambda when
 // profiling is on, otherwise just runs it.
+template <typename Fn>
+void timed(hsolve_handle* h, const char* name, int launches, Fn&& fn);
+
+// Per-level variant: phases are reported as "<name>.L<level>" when the
+// handle records per-level detail.
+template <typename Fn>
+void timed_lv(hsolve_handle* h, const char* name, int level, int launches, Fn&& fn) {
+  if (h->profiling && h->profile_levels) {
+    std::string nm = std::string(name) + ".L" + std::to_string(level);
+    timed(h, nm.c_str(), launches, fn);
+  } else {
+    timed(h, name, launches, fn);
+  }
+}
+
 template <typename Fn>
 void timed(hsolve_handle* h, const char* name, int launches, Fn&& fn) {
   h->launches += launches;
@@ -501,32 +520,56 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     real* ws = h->ws.as<real>();
     const int64_t* d_gptr = reinterpret_cast<const int64_t*>(d + o_gptr);
     const int* d_gstr = reinterpret_cast<const int*>(d + o_gstr);
-    timed(h, "prep", 1, [&] {
+    long long* dbg = nullptr;
+    if (h->profiling && h->profile_levels) {
+      h->dbg.ensure(sizeof(long long) * 8 * (size_t)nt);
+      HS_CUDA(cudaMemsetAsync(h->dbg.p, 0, sizeof(long long) * 8 * (size_t)nt, h->st));
+      dbg = h->dbg.as<long long>();
+    }
+    timed_lv(h, "prep", level, 1, [&] {
       Launch<real>::prep(reinterpret_cast<const PrepTask*>(d + o_prep), nt, arena, fac, ws,
                          h->wsd.as<double>(), d_gptr, d_gstr, rank, eps, sym ? 1 : 0,
-                         h->opts.max_rank, maxm, h->d_err.as<DevError>(), level, h->st);
+                         h->opts.max_rank, maxm, h->d_err.as<DevError>(), level, dbg, h->st);
     });
-    timed(h, "gemm_coarse", sym ? 1 : 2, [&] {
+    if (dbg) {
+      // per checkpoint interval: the slowest cluster of the class, in ms at
+      // the 2.07 GHz maximum SM clock
+      std::vector<long long> hd(8 * (size_t)nt);
+      HS_CUDA(cudaMemcpy(hd.data(), dbg, sizeof(long long) * hd.size(), cudaMemcpyDeviceToHost));
+      static const char* nm[7] = {"chol", "gather", "cpqr", "inverse", "complement", "T_C",
+                                  "F_tail"};
+      for (int q = 0; q < 7; q++) {
+        long long mx = 0;
+        for (int t = 0; t < nt; t++) {
+          long long a = hd[t * 8 + q], b2 = 0;
+          for (int r = q + 1; r < 8 && !b2; r++) b2 = hd[t * 8 + r];
+          if (a && b2 > a) mx = std::max(mx, b2 - a);
+        }
+        std::string key = std::string("prep.") + nm[q] + ".L" + std::to_string(level);
+        phase_add(h, key.c_str(), mx / 2.07e6, 0);
+      }
+    }
+    timed_lv(h, "gemm_coarse", level, sym ? 1 : 2, [&] {
       Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gY), (int)gY.size(), maxm,
                                 maxnw, fac, fac, arena, d_gptr, d_gstr, rank, h->st);
       if (!sym)
         Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gXT), (int)gXT.size(),
                                   maxm, maxnw, fac, fac, arena, d_gptr, d_gstr, rank, h->st);
     });
-    timed(h, "gemm_fill", sym ? 1 : 2, [&] {
+    timed_lv(h, "gemm_fill", level, sym ? 1 : 2, [&] {
       Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gE), (int)gE.size(), maxm,
                                 maxnwf, ws, ws, arena, d_gptr, d_gstr, rank, h->st);
       if (!sym)
         Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gE2), (int)gE2.size(),
                                   maxm, maxnwf, ws, ws, arena, d_gptr, d_gstr, rank, h->st);
     });
-    timed(h, "scatter", 2, [&] {
+    timed_lv(h, "scatter", level, 2, [&] {
       Launch<real>::scatter(reinterpret_cast<const ScatterSeg*>(d + o_segN), (int)segN.size(),
                             maxw_seg, fac, arena, rank, h->st);
       Launch<real>::scatter(reinterpret_cast<const ScatterSeg*>(d + o_segW), (int)segW.size(),
                             maxw_seg, ws, arena, rank, h->st);
     });
-    timed(h, "schur", 1, [&] {
+    timed_lv(h, "schur", level, 1, [&] {
       Launch<real>::schur(reinterpret_cast<const SchurTask*>(d + o_sch), (int)sch.size(), maxnw,
                           fac, arena, reinterpret_cast<const int*>(d + o_smap),
                           reinterpret_cast<const int64_t*>(d + o_sbase),
@@ -570,8 +613,6 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   // ---- apply records and maps for this level
   Blob b;
   FL.recs.alloc(sizeof(ApplyRec) * std::max(nc, 1));
-  HS_CUDA(cudaMemcpyAsync(FL.recs.p, recs.data(), sizeof(ApplyRec) * nc, cudaMemcpyHostToDevice,
-                          h->st));
   FL.vmap.alloc(sizeof(int64_t) * std::max<size_t>(vmap.size(), 1));
   if (!vmap.empty())
     HS_CUDA(cudaMemcpyAsync(FL.vmap.p, vmap.data(), sizeof(int64_t) * vmap.size(),
@@ -579,15 +620,25 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   std::vector<int> ids;
   FL.cls_off.clear();
   FL.cls_maxm.clear();
+  FL.cls_maxnw.clear();
+  FL.part_elems = 0;
   for (auto& S : FL.cls) {
     FL.cls_off.push_back((int)ids.size());
-    int mx = 1;
+    int mx = 1, mw = 0;
     for (int s : S) {
       ids.push_back(s);
-      mx = std::max(mx, std::max(recs[s].m, recs[s].nw));
+      mx = std::max(mx, recs[s].m);
+      mw = std::max(mw, recs[s].nw);
+      const int f = recs[s].m - recs[s].k;
+      const int nchunk = (recs[s].nw + 63) / 64;
+      recs[s].part = FL.part_elems;
+      FL.part_elems += (int64_t)nchunk * std::max(f, 0);
     }
     FL.cls_maxm.push_back(mx);
+    FL.cls_maxnw.push_back(mw);
   }
+  HS_CUDA(cudaMemcpyAsync(FL.recs.p, recs.data(), sizeof(ApplyRec) * nc, cudaMemcpyHostToDevice,
+                          h->st));
   FL.cls_off.push_back((int)ids.size());
   FL.ids.alloc(sizeof(int) * std::max<size_t>(ids.size(), 1));
   if (!ids.empty())
@@ -759,8 +810,13 @@ template <typename real>
 void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int64_t ld) {
   const int L = (int)h->F.size();
   for (auto& F : h->F) {
-    size_t need = sizeof(real) * (size_t)std::max<int64_t>(F->P.voff[F->P.nclu], 1) * nrhs;
-    if (F->vec.bytes < need) F->vec.alloc(need);
+    if (F->vec_nrhs < nrhs) {
+      const size_t nv = sizeof(real) * (size_t)std::max<int64_t>(F->P.voff[F->P.nclu], 1) * nrhs;
+      F->vec.alloc(nv);
+      F->zvec.alloc(nv);
+      F->part.alloc(sizeof(real) * (size_t)std::max<int64_t>(F->part_elems, 1) * nrhs);
+      F->vec_nrhs = nrhs;
+    }
   }
   FLevel& F0 = *h->F[0];
   const int64_t n0 = F0.P.voff[F0.P.nclu];
@@ -770,8 +826,9 @@ void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int6
     const int64_t nl = std::max<int64_t>(F.P.voff[F.P.nclu], 1);
     for (size_t c = 0; c < F.cls.size(); c++)
       Launch<real>::apply_fwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
-                              (int)F.cls[c].size(), F.fac.as<real>(), F.vmap.as<int64_t>(),
-                              F.vec.as<real>(), nl, nrhs, F.cls_maxm[c], h->st);
+                              (int)F.cls[c].size(), F.cls_maxm[c], F.cls_maxnw[c],
+                              F.fac.as<real>(), F.vmap.as<int64_t>(), F.vec.as<real>(),
+                              F.zvec.as<real>(), nl, nrhs, h->st);
     if (l + 1 < L) {
       FLevel& G = *h->F[l + 1];
       const int64_t ng = std::max<int64_t>(G.P.voff[G.P.nclu], 1);
@@ -790,8 +847,9 @@ void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int6
     }
     for (int c = (int)F.cls.size() - 1; c >= 0; c--)
       Launch<real>::apply_bwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
-                              (int)F.cls[c].size(), F.fac.as<real>(), F.vmap.as<int64_t>(),
-                              F.vec.as<real>(), nl, nrhs, F.cls_maxm[c], h->st);
+                              (int)F.cls[c].size(), F.cls_maxm[c], F.cls_maxnw[c],
+                              F.fac.as<real>(), F.vmap.as<int64_t>(), F.vec.as<real>(),
+                              F.zvec.as<real>(), F.part.as<real>(), nl, nrhs, h->st);
   }
   Launch<real>::perm_out(h->d_perm.as<int64_t>(), h->n, F0.vec.as<real>(), n0, out, ld, nrhs, h->st);
 }
@@ -1356,6 +1414,7 @@ hsolve_status hsolve_get_phase_times(const hsolve_handle* h, hsolve_phase_time* 
 hsolve_status hsolve_set_profiling(hsolve_handle* h, int on) {
   if (!h) return HSOLVE_ERR_ARG;
   h->profiling = on != 0;
+  h->profile_levels = on > 1;
   return HSOLVE_OK;
 }
 

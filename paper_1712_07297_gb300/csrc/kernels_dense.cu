@@ -9,7 +9,9 @@
 // Matrices are column-major.  `real` is the storage/compute type of the
 // factorization (double in float64 mode, float in the mixed modes); squared
 // column norms of the rank-revealing QR and its rank decision are always
-// accumulated in double.
+// accumulated in double.  The factor of A_ss and A_ss^{-1} live in shared
+// memory when they fit (the host sizes the dynamic shared memory per class);
+// everything else is in a per-cluster global workspace that stays in L2.
 #include <cfloat>
 #include <climits>
 #include <cmath>
@@ -22,34 +24,88 @@ namespace {
 
 constexpr int kPrepThreads = 256;
 constexpr double kPivotTieRtol = 1e-10;
+constexpr int GT = 64, GK = 16;  // CTA GEMM tile and inner chunk
 
 template <typename real>
-__device__ __forceinline__ real rsqrt_(real x);
+__device__ __forceinline__ real sqrt_(real x);
 template <>
-__device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 template <>
-__device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 
-// C (M x N, ldc) = alpha * op(A) * op(B) + beta * C, whole CTA.
+// C (M x N, ldc) = alpha * op(A) * op(B) + beta * C, whole CTA (256 threads,
+// 64 x 64 output tiles, 4 x 4 outputs per thread, inner chunks of 16 staged
+// in shared memory `sh` of 2 * 16 * 65 reals).  C must not alias A or B.
 template <typename real>
 __device__ void cta_gemm(int M, int N, int K, const real* A, int lda, bool ta, const real* B,
-                         int ldb, bool tb, real* C, int ldc, real alpha, real beta) {
-  for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
-    int i = idx % M, j = idx / M;
-    real acc = 0;
-    if (!ta && !tb) {
-      for (int l = 0; l < K; l++) acc += A[i + (int64_t)l * lda] * B[l + (int64_t)j * ldb];
-    } else if (ta && !tb) {
-      for (int l = 0; l < K; l++) acc += A[l + (int64_t)i * lda] * B[l + (int64_t)j * ldb];
-    } else if (!ta && tb) {
-      for (int l = 0; l < K; l++) acc += A[i + (int64_t)l * lda] * B[j + (int64_t)l * ldb];
-    } else {
-      for (int l = 0; l < K; l++) acc += A[l + (int64_t)i * lda] * B[j + (int64_t)l * ldb];
+                         int ldb, bool tb, real* C, int ldc, real alpha, real beta, real* sh) {
+  real* As = sh;
+  real* Bs = sh + GK * (GT + 1);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  for (int i0 = 0; i0 < M; i0 += GT)
+    for (int j0 = 0; j0 < N; j0 += GT) {
+      real acc[4][4];
+#pragma unroll
+      for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[p][q] = 0;
+      for (int l0 = 0; l0 < K; l0 += GK) {
+        for (int e = threadIdx.x; e < GT * GK; e += blockDim.x) {
+          int i, l;
+          if (!ta) {
+            i = e % GT;
+            l = e / GT;
+          } else {
+            l = e % GK;
+            i = e / GK;
+          }
+          int gi = i0 + i, gl = l0 + l;
+          real v = 0;
+          if (gi < M && gl < K) v = ta ? A[gl + (int64_t)gi * lda] : A[gi + (int64_t)gl * lda];
+          As[l * (GT + 1) + i] = v;
+        }
+        for (int e = threadIdx.x; e < GT * GK; e += blockDim.x) {
+          int l, j;
+          if (!tb) {
+            l = e % GK;
+            j = e / GK;
+          } else {
+            j = e % GT;
+            l = e / GT;
+          }
+          int gl = l0 + l, gj = j0 + j;
+          real v = 0;
+          if (gl < K && gj < N) v = tb ? B[gj + (int64_t)gl * ldb] : B[gl + (int64_t)gj * ldb];
+          Bs[l * (GT + 1) + j] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < GK; l++) {
+          real a[4], b[4];
+#pragma unroll
+          for (int p = 0; p < 4; p++) {
+            a[p] = As[l * (GT + 1) + ty + 16 * p];
+            b[p] = Bs[l * (GT + 1) + tx + 16 * p];
+          }
+#pragma unroll
+          for (int p = 0; p < 4; p++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[p][q] += a[p] * b[q];
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          int gi = i0 + ty + 16 * p, gj = j0 + tx + 16 * q;
+          if (gi < M && gj < N) {
+            real c = alpha * acc[p][q];
+            if (beta != real(0)) c += beta * C[gi + (int64_t)gj * ldc];
+            C[gi + (int64_t)gj * ldc] = c;
+          }
+        }
     }
-    real c = alpha * acc;
-    if (beta != real(0)) c += beta * C[i + (int64_t)j * ldc];
-    C[i + (int64_t)j * ldc] = c;
-  }
   __syncthreads();
 }
 
@@ -62,9 +118,18 @@ __device__ void cta_copy(int M, int N, const real* A, int64_t lda, real* B, int6
   __syncthreads();
 }
 
+// Zero the strict upper (upper=true) or strict lower part of an n x n matrix.
+template <typename real>
+__device__ void cta_zero_tri(int n, real* A, int lda, bool upper) {
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    int i = idx % n, j = idx / n;
+    if (upper ? (i < j) : (i > j)) A[i + (int64_t)j * lda] = 0;
+  }
+  __syncthreads();
+}
+
 template <typename real>
 __device__ void cta_identity(int M, int N, int diag_off, real* A, int lda) {
-  // A[i, j] = (i == j + diag_off)
   for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
     int i = idx % M, j = idx / M;
     A[i + (int64_t)j * lda] = (i == j + diag_off) ? real(1) : real(0);
@@ -72,26 +137,22 @@ __device__ void cta_identity(int M, int N, int diag_off, real* A, int lda) {
   __syncthreads();
 }
 
-// In-place lower Cholesky A = L L^T.  Returns false (on every thread) for a
-// non-positive pivot.
+// In-place lower Cholesky A = L L^T (lower triangle).  Returns false on every
+// thread for a non-positive pivot.
 template <typename real>
 __device__ bool cta_cholesky(int n, real* A, int lda, int* sflag) {
   for (int j = 0; j < n; j++) {
     if (threadIdx.x == 0) {
       real d = A[j + (int64_t)j * lda];
-      if (!(d > real(0))) {
-        *sflag = 1;
-      } else {
-        A[j + (int64_t)j * lda] = rsqrt_(d);
-      }
+      if (!(d > real(0))) *sflag = 1;
+      else A[j + (int64_t)j * lda] = sqrt_(d);
     }
     __syncthreads();
     if (*sflag) return false;
-    real djj = A[j + (int64_t)j * lda];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (int64_t)j * lda] /= djj;
+    const real rd = real(1) / A[j + (int64_t)j * lda];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (int64_t)j * lda] *= rd;
     __syncthreads();
-    int t = n - j - 1;
-    // trailing update of the lower triangle
+    const int t = n - j - 1;
     for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
       int i = j + 1 + idx % t, l = j + 1 + idx / t;
       if (i >= l) A[i + (int64_t)l * lda] -= A[i + (int64_t)j * lda] * A[l + (int64_t)j * lda];
@@ -105,34 +166,34 @@ __device__ bool cta_cholesky(int n, real* A, int lda, int* sflag) {
 // swapped with j at step j.  Near-ties (|a| >= (1 - 1e-10) max) go to the
 // lowest row.  Returns false for an exactly zero pivot column.
 template <typename real>
-__device__ bool cta_lu(int n, real* A, int lda, int* piv, real* red_v, int* red_i,
+__device__ bool cta_lu(int n, real* A, int lda, int* piv, double* red_d, int* red_i,
                        int* sflag) {
   for (int j = 0; j < n; j++) {
-    // column maximum
-    real mx = 0;
-    for (int i = j + threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(A[i + (int64_t)j * lda]));
-    red_v[threadIdx.x] = mx;
+    double mx = 0;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x)
+      mx = fmax(mx, fabs((double)A[i + (int64_t)j * lda]));
+    red_d[threadIdx.x] = mx;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) red_v[threadIdx.x] = fmax(red_v[threadIdx.x], red_v[threadIdx.x + s]);
+      if (threadIdx.x < s) red_d[threadIdx.x] = fmax(red_d[threadIdx.x], red_d[threadIdx.x + s]);
       __syncthreads();
     }
-    mx = red_v[0];
+    mx = red_d[0];
     __syncthreads();
     int best = n;
     for (int i = j + threadIdx.x; i < n; i += blockDim.x)
-      if (fabs(A[i + (int64_t)j * lda]) >= (real)(1.0 - kPivotTieRtol) * mx && i < best) best = i;
+      if (fabs((double)A[i + (int64_t)j * lda]) >= (1.0 - kPivotTieRtol) * mx && i < best) best = i;
     red_i[threadIdx.x] = best;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
       if (threadIdx.x < s) red_i[threadIdx.x] = min(red_i[threadIdx.x], red_i[threadIdx.x + s]);
       __syncthreads();
     }
-    int p = red_i[0];
+    const int p = red_i[0];
     __syncthreads();
     if (threadIdx.x == 0) {
       piv[j] = p;
-      if (!(mx > real(0))) *sflag = 1;
+      if (!(mx > 0.0)) *sflag = 1;
     }
     __syncthreads();
     if (*sflag) return false;
@@ -143,10 +204,10 @@ __device__ bool cta_lu(int n, real* A, int lda, int* piv, real* red_v, int* red_
         A[p + (int64_t)c * lda] = t;
       }
     __syncthreads();
-    real d = A[j + (int64_t)j * lda];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (int64_t)j * lda] /= d;
+    const real rd = real(1) / A[j + (int64_t)j * lda];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (int64_t)j * lda] *= rd;
     __syncthreads();
-    int t = n - j - 1;
+    const int t = n - j - 1;
     for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
       int i = j + 1 + idx % t, l = j + 1 + idx / t;
       A[i + (int64_t)l * lda] -= A[i + (int64_t)j * lda] * A[j + (int64_t)l * lda];
@@ -156,40 +217,43 @@ __device__ bool cta_lu(int n, real* A, int lda, int* piv, real* red_v, int* red_
   return true;
 }
 
-// Linv = L^{-1} for lower triangular L (unit diagonal if `unit`), column
-// parallel forward substitution.  Linv is n x n, upper part zeroed.
+// In-place inverse of a lower triangular matrix (unit diagonal if `unit`,
+// diagonal then left untouched), column by column from the last: the
+// trailing part is already inverted when column j is formed.  tmp: n reals.
 template <typename real>
-__device__ void cta_tri_inv_lower(int n, const real* L, int ldl, bool unit, real* Li, int ldi) {
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    real* y = Li + (int64_t)c * ldi;
-    for (int i = 0; i < c; i++) y[i] = 0;
-    y[c] = unit ? real(1) : real(1) / L[c + (int64_t)c * ldl];
-    for (int i = c + 1; i < n; i++) {
+__device__ void cta_trtri_lower(int n, real* L, int ld, bool unit, real* tmp) {
+  for (int j = n - 1; j >= 0; j--) {
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) tmp[i] = L[i + (int64_t)j * ld];
+    if (threadIdx.x == 0 && !unit) L[j + (int64_t)j * ld] = real(1) / L[j + (int64_t)j * ld];
+    __syncthreads();
+    const real d = unit ? real(1) : L[j + (int64_t)j * ld];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
       real acc = 0;
-      for (int l = c; l < i; l++) acc += L[i + (int64_t)l * ldl] * y[l];
-      y[i] = unit ? -acc : -acc / L[i + (int64_t)i * ldl];
+      for (int l = j + 1; l <= i; l++) acc += (l == i && unit ? real(1) : L[i + (int64_t)l * ld]) * tmp[l];
+      L[i + (int64_t)j * ld] = -acc * d;
     }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
-// Ui = U^{-1} for upper triangular U, column-parallel back substitution.
+// In-place inverse of an upper triangular matrix, column by column from the
+// first.  tmp: n reals.
 template <typename real>
-__device__ void cta_tri_inv_upper(int n, const real* U, int ldu, real* Ui, int ldi) {
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    real* y = Ui + (int64_t)c * ldi;
-    for (int i = c + 1; i < n; i++) y[i] = 0;
-    y[c] = real(1) / U[c + (int64_t)c * ldu];
-    for (int i = c - 1; i >= 0; i--) {
+__device__ void cta_trtri_upper(int n, real* U, int ld, real* tmp) {
+  for (int j = 0; j < n; j++) {
+    for (int i = threadIdx.x; i < j; i += blockDim.x) tmp[i] = U[i + (int64_t)j * ld];
+    if (threadIdx.x == 0) U[j + (int64_t)j * ld] = real(1) / U[j + (int64_t)j * ld];
+    __syncthreads();
+    const real d = U[j + (int64_t)j * ld];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
       real acc = 0;
-      for (int l = i + 1; l <= c; l++) acc += U[i + (int64_t)l * ldu] * y[l];
-      y[i] = -acc / U[i + (int64_t)i * ldu];
+      for (int l = i; l < j; l++) acc += U[i + (int64_t)l * ld] * tmp[l];
+      U[i + (int64_t)j * ld] = -acc * d;
     }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
-// Block reductions over the first `cnt` entries handled by all threads.
 __device__ double cta_max_d(double v, double* red) {
   red[threadIdx.x] = v;
   __syncthreads();
@@ -214,30 +278,47 @@ __device__ int cta_min_i(int v, int* red) {
   return r;
 }
 
-// Householder QR of the m x c matrix G (in place, ld m).  With `pivot`,
-// columns are pivoted by largest remaining norm (recomputed every step,
-// near-ties to the lowest original index, orig[] tracks original indices),
-// stopping at |r_jj| <= eps |r_11| (eps > 0), at |r_jj| <= floor (rounding
-// noise of a block that is zero in exact arithmetic), at an all-zero
-// remainder or at kmax steps.  Householder vectors stay in G below the diagonal (v_j in
-// G[j:m, j]); tau[j] holds 2 / v^T v.  Returns the number of steps k.
-template <typename real>
+__device__ double cta_sum_d(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Householder QR of the m x c matrix G (in place).  Element (i, q) sits at
+// G[i * ldg + q] when RowMajor (one thread per column then reads coalesced
+// across a warp), else at G[i + q * ldg].  With `pivot`, columns are pivoted
+// by largest remaining norm (recomputed every step, near-ties to the lowest
+// original index, orig[] tracks original indices), stopping at
+// |r_jj| <= eps |r_11| (eps > 0), at |r_jj| <= floor (rounding noise of a
+// block that is zero in exact arithmetic), at an all-zero remainder or at
+// kmax steps.  Householder vectors stay in G (v_j in rows j..m of column j);
+// tau[j] = 2 / v^T v.  vsh: m reals of shared memory.  Returns the number of
+// steps.
+template <typename real, bool RowMajor>
 __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, double* orig,
                                   real* tau, bool pivot, double eps, int kmax, double floor,
-                                  double* red_d, int* red_i) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  // initial squared norms
-  for (int q = warp; q < c; q += nwarp) {
-    const real* col = G + (int64_t)q * ldg;
-    double s = 0;
-    for (int i = lane; i < m; i += 32) s += (double)col[i] * (double)col[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
+                                  double* red_d, int* red_i, real* vsh) {
+  auto at = [&](int i, int q) -> real& {
+    return RowMajor ? G[(int64_t)i * ldg + q] : G[i + (int64_t)q * ldg];
+  };
+  if (pivot) {
+    for (int q = threadIdx.x; q < c; q += blockDim.x) {
+      double s = 0;
+      for (int i = 0; i < m; i++) {
+        double v = at(i, q);
+        s += v * v;
+      }
       nrm2[q] = s;
       orig[q] = q;
     }
+    __syncthreads();
   }
-  __syncthreads();
   double r11 = 0;
   int k = 0;
   const int steps = min(m, c);
@@ -253,7 +334,6 @@ __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, 
       for (int t = j + threadIdx.x; t < c; t += blockDim.x)
         if (nrm2[t] >= (1.0 - kPivotTieRtol) * mx) best = min(best, (int)orig[t]);
       best = cta_min_i(best, red_i);
-      // locate the column holding original index `best`
       for (int t = j + threadIdx.x; t < c; t += blockDim.x)
         if ((int)orig[t] == best) red_i[blockDim.x] = t;
       __syncthreads();
@@ -265,12 +345,10 @@ __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, 
       if (eps > 0.0 && r <= eps * r11) break;
       if (j >= kmax) break;
       if (q != j) {
-        real* a = G + (int64_t)j * ldg;
-        real* b = G + (int64_t)q * ldg;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
-          real t = a[i];
-          a[i] = b[i];
-          b[i] = t;
+          real t = at(i, j);
+          at(i, j) = at(i, q);
+          at(i, q) = t;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -285,47 +363,82 @@ __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, 
       }
     } else {
       if (j >= kmax) break;
-      // norm of the current column over rows j..m
       double s = 0;
       for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
-        double x = G[i + (int64_t)j * ldg];
+        double x = at(i, j);
         s += x * x;
       }
-      red_d[threadIdx.x] = s;
-      __syncthreads();
-      for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) red_d[threadIdx.x] += red_d[threadIdx.x + st];
-        __syncthreads();
-      }
-      r = sqrt(red_d[0]);
-      __syncthreads();
+      r = sqrt(cta_sum_d(s, red_d));
     }
     // reflector v = x - beta e1, beta = -sign(x0) ||x||, tau = 2 / v^T v
-    real* x = G + (int64_t)j * ldg;
-    double x0 = (double)x[j];
-    double beta = (x0 >= 0.0) ? -r : r;
-    double tj = (r > 0.0) ? 1.0 / (r * (r + fabs(x0))) : 0.0;
+    const double x0 = (double)at(j, j);
+    const double beta = (x0 >= 0.0) ? -r : r;
+    const double tj = (r > 0.0) ? 1.0 / (r * (r + fabs(x0))) : 0.0;
+    __syncthreads();
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) vsh[i] = (i == j) ? (real)(x0 - beta) : at(i, j);
     __syncthreads();
     if (threadIdx.x == 0) {
-      x[j] = (real)(x0 - beta);
+      at(j, j) = (real)(x0 - beta);
       tau[j] = (real)tj;
     }
-    __syncthreads();
-    // apply to the remaining columns; recompute their norms over rows j+1..m
-    for (int t = j + 1 + warp; t < c; t += nwarp) {
-      real* col = G + (int64_t)t * ldg;
-      real w = 0;
-      for (int i = j + lane; i < m; i += 32) w += x[i] * col[i];
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      w *= (real)tj;
-      double s = 0;
-      for (int i = j + lane; i < m; i += 32) {
-        real v = col[i] - w * x[i];
-        col[i] = v;
-        if (i > j) s += (double)v * (double)v;
+    const real rt = (real)tj;
+    // apply to the remaining columns, CB columns per thread and RB rows per
+    // batch of independent loads (memory-level parallelism); recompute the
+    // squared norms over rows j+1..m
+    constexpr int CB = 4, RB = 4;
+    const int nth = blockDim.x;
+    for (int t0 = j + 1 + threadIdx.x; t0 < c; t0 += nth * CB) {
+      real w[CB];
+      bool ok[CB];
+#pragma unroll
+      for (int g = 0; g < CB; g++) {
+        w[g] = 0;
+        ok[g] = (t0 + g * nth) < c;
       }
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) nrm2[t] = s;
+      for (int i = j; i < m; i += RB) {
+        real x[RB][CB];
+#pragma unroll
+        for (int rr = 0; rr < RB; rr++)
+#pragma unroll
+          for (int g = 0; g < CB; g++)
+            x[rr][g] = (ok[g] && i + rr < m) ? at(i + rr, t0 + g * nth) : real(0);
+#pragma unroll
+        for (int rr = 0; rr < RB; rr++) {
+          const real vi = (i + rr < m) ? vsh[i + rr] : real(0);
+#pragma unroll
+          for (int g = 0; g < CB; g++) w[g] += vi * x[rr][g];
+        }
+      }
+      double sq[CB];
+#pragma unroll
+      for (int g = 0; g < CB; g++) {
+        w[g] *= rt;
+        sq[g] = 0;
+      }
+      for (int i = j; i < m; i += RB) {
+        real x[RB][CB];
+#pragma unroll
+        for (int rr = 0; rr < RB; rr++)
+#pragma unroll
+          for (int g = 0; g < CB; g++)
+            x[rr][g] = (ok[g] && i + rr < m) ? at(i + rr, t0 + g * nth) : real(0);
+#pragma unroll
+        for (int rr = 0; rr < RB; rr++) {
+          if (i + rr >= m) break;
+          const real vi = vsh[i + rr];
+#pragma unroll
+          for (int g = 0; g < CB; g++) {
+            if (!ok[g]) continue;
+            const real v = x[rr][g] - w[g] * vi;
+            at(i + rr, t0 + g * nth) = v;
+            if (i + rr > j) sq[g] += (double)v * (double)v;
+          }
+        }
+      }
+      if (pivot)
+#pragma unroll
+        for (int g = 0; g < CB; g++)
+          if (ok[g]) nrm2[t0 + g * nth] = sq[g];
     }
     __syncthreads();
     k = j + 1;
@@ -334,25 +447,66 @@ __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, 
   return k;
 }
 
-// Q[:, c0:c0+ncols] of Q = H_0 .. H_{k-1}: out (m x ncols, ld m) starts as
-// the identity columns c0.. and receives the reflectors in reverse order.
-template <typename real>
+// Q[:, c0:c0+ncols] of Q = H_0 .. H_{k-1}: out (m x ncols) starts as the
+// identity columns c0.. and receives the reflectors in reverse order.
+template <typename real, bool RowMajor>
 __device__ void cta_form_q(int m, int k, const real* V, int ldv, const real* tau, int c0,
-                           int ncols, real* out, int ldo) {
+                           int ncols, real* out, int ldo, real* vsh) {
   cta_identity<real>(m, ncols, c0, out, ldo);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  constexpr int RB = 8;
   for (int j = k - 1; j >= 0; j--) {
-    const real* v = V + (int64_t)j * ldv;
-    real tj = tau[j];
-    for (int t = warp; t < ncols; t += nwarp) {
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x)
+      vsh[i] = RowMajor ? V[(int64_t)i * ldv + j] : V[i + (int64_t)j * ldv];
+    __syncthreads();
+    const real tj = tau[j];
+    for (int t = threadIdx.x; t < ncols; t += blockDim.x) {
       real* col = out + (int64_t)t * ldo;
       real w = 0;
-      for (int i = j + lane; i < m; i += 32) w += v[i] * col[i];
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      for (int i = j; i < m; i += RB) {
+        real x[RB];
+#pragma unroll
+        for (int rr = 0; rr < RB; rr++) x[rr] = (i + rr < m) ? col[i + rr] : real(0);
+#pragma unroll
+        for (int rr = 0; rr < RB; rr++)
+          if (i + rr < m) w += vsh[i + rr] * x[rr];
+      }
       w *= tj;
-      for (int i = j + lane; i < m; i += 32) col[i] -= w * v[i];
+      for (int i = j; i < m; i += RB) {
+        real x[RB];
+#pragma unroll
+        for (int rr = 0; rr < RB; rr++) x[rr] = (i + rr < m) ? col[i + rr] : real(0);
+#pragma unroll
+        for (int rr = 0; rr < RB; rr++)
+          if (i + rr < m) col[i + rr] = x[rr] - w * vsh[i + rr];
+      }
     }
     __syncthreads();
+  }
+}
+
+// Column permutation of the LU inverse: (X P)[:, c] = X[:, pos(c)], pos(c) =
+// row of P A holding original row c after the swaps piv[0..n-1] in order.
+template <typename real>
+__device__ void cta_permute_cols(int n, const int* piv, const real* X, int ldx, real* Y, int ldy) {
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    int pos = c;
+    for (int j = 0; j < n; j++) {
+      if (piv[j] == pos) pos = j;
+      else if (j == pos) pos = piv[j];
+    }
+    for (int i = 0; i < n; i++) Y[i + (int64_t)c * ldy] = X[i + (int64_t)pos * ldx];
+  }
+  __syncthreads();
+}
+
+template <typename real>
+__device__ void report(DevError* err, int code, int s, int level, int* rank, int m) {
+  if (threadIdx.x == 0) {
+    if (atomicCAS(&err->code, 0, code) == 0) {
+      err->cluster = s;
+      err->level = level;
+    }
+    rank[s] = m;  // leave the cluster untouched downstream
   }
 }
 
@@ -361,30 +515,43 @@ __global__ void __launch_bounds__(kPrepThreads)
 prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* __restrict__ fac,
             real* __restrict__ ws_all, double* __restrict__ wsd_all,
             const int64_t* __restrict__ gptr, const int* __restrict__ gstr, int* rank,
-            double eps, double noise_rtol, int sym, int max_rank, DevError* err, int level) {
+            double eps, double noise_rtol, int sym, int max_rank, int smem_mats, int smem_m,
+            DevError* err, int level, long long* dbg) {
   __shared__ double red_d[kPrepThreads];
   __shared__ int red_i[kPrepThreads + 1];
   __shared__ int sflag;
   __shared__ int s_ncol;
   __shared__ double s_amax;
+  __shared__ real gsh[2 * GK * (GT + 1)];
+  extern __shared__ unsigned char dsm[];
   const PrepTask tk = tasks[blockIdx.x];
   const int m = tk.m;
+  // optional per-phase clock stamps (profiling): dbg[task * 8 + checkpoint]
+  long long* stamp = dbg ? dbg + (int64_t)blockIdx.x * 8 : nullptr;
+  auto mark = [&](int i) {
+    if (stamp && threadIdx.x == 0) stamp[i] = clock64();
+  };
+  mark(0);
   if (threadIdx.x == 0) sflag = 0;
   __syncthreads();
   const int64_t mm = (int64_t)m * m;
   real* ws = ws_all + tk.ws;
-  real* W_A = ws;                 // A_ss, then its factor
-  real* W_B = W_A + mm;           // A_ss^{-1}
-  real* W_U = W_B + mm;           // U (m x k)
-  real* W_X = W_U + mm;           // X = B U, then its reflectors
-  real* W_V = W_X + mm;           // V_L (m x f)
-  real* W_T = W_V + mm;           // [U V_L]^T B
-  real* W_F = W_T + mm;           // F, then its factor
-  real* W_L = W_F + mm;           // inverse factor(s) of F
-  real* W_C = W_L + mm;           // C = U^T B U
-  real* W_R = W_C + mm;           // general: V_R, then T_R = B [U V_R]
-  real* W_S = W_R + mm;           // general: scratch
-  real* W_G = W_S + mm;           // G (m x ncolG)
+  real* smat = reinterpret_cast<real*>(dsm);
+  real* vsh = smat + (int64_t)smem_mats * smem_m * smem_m;  // m reals
+  real* tsh = vsh + smem_m;                                  // m reals
+  real* W_A = smem_mats >= 1 ? smat : ws;                               // A_ss -> factor -> inverse factor
+  real* W_B = smem_mats >= 2 ? smat + (int64_t)smem_m * smem_m : ws + mm;  // A_ss^{-1}
+  // [U V_L] as one m x m matrix: U in columns 0..k, V_L in columns k..m
+  real* W_U = smem_mats >= 3 ? smat + 2 * (int64_t)smem_m * smem_m : ws + 2 * mm;
+  real* W_X = ws + 3 * mm;   // X = B U, then its reflectors
+  real* W_V = W_U + (int64_t)0;  // V_L = columns k..m of W_U (set below)
+  real* W_T = ws + 4 * mm;   // [U V_L]^T B
+  real* W_F = W_T + mm;      // F, then its factor / inverse factor (general)
+  real* W_L = W_F + mm;      // general: L^{-1} P, (U_F^{-1})
+  real* W_C = W_L + mm;      // C = U^T B U
+  real* W_R = W_C + mm;      // general: V_R
+  real* W_S = W_R + mm;      // general: scratch
+  real* W_G = W_S + mm;      // G (m x ncolG)
   double* nrm2 = wsd_all + tk.wsd;
   double* orig = nrm2 + tk.ncolG;
   real* tau = reinterpret_cast<real*>(orig + tk.ncolG);
@@ -392,7 +559,7 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
   int* piv = reinterpret_cast<int*>(tau2 + m);
   real* T = fac + tk.T;
 
-  // ---- gather A_ss, its largest magnitude (scale of the noise floor), factor
+  // ---- A_ss, its largest magnitude (scale of the noise floor), its factor
   cta_copy<real>(m, m, arena + tk.a_ss, tk.ld, W_A, m);
   {
     double mx = 0;
@@ -401,168 +568,168 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
     if (threadIdx.x == 0) s_amax = mx;
     __syncthreads();
   }
-  bool ok = sym ? cta_cholesky<real>(m, W_A, m, &sflag)
-                : cta_lu<real>(m, W_A, m, piv, reinterpret_cast<real*>(red_d), red_i, &sflag);
+  const bool ok = sym ? cta_cholesky<real>(m, W_A, m, &sflag)
+                      : cta_lu<real>(m, W_A, m, piv, red_d, red_i, &sflag);
   if (!ok) {
-    if (threadIdx.x == 0) {
-      if (atomicCAS(&err->code, 0, sym ? (int)HSOLVE_ERR_NOT_SPD : (int)HSOLVE_ERR_SINGULAR) == 0) {
-        err->cluster = tk.s;
-        err->level = level;
-      }
-      rank[tk.s] = tk.m;  // leave the cluster untouched downstream
-    }
+    report<real>(err, sym ? (int)HSOLVE_ERR_NOT_SPD : (int)HSOLVE_ERR_SINGULAR, tk.s, level, rank, m);
     return;
   }
 
-  // ---- gather the nonzero fill columns into G (Eq. lra input)
+  mark(1);
+  // ---- gather the nonzero fill columns into G (Eq. lra input), row-major
   {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    // pass 1: flag nonzero columns (stored in nrm2 temporarily)
-    for (int q = warp; q < tk.ncolG; q += nwarp) {
+    const int nc = tk.ncolG;
+    // flag nonzero columns: one thread per column, batched independent loads
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
       const int64_t p = gptr[tk.gcol + q];
       const int st = gstr[tk.gcol + q];
       bool nz = false;
-      for (int i = lane; i < m; i += 32) nz |= (arena[p + (int64_t)i * st] != real(0));
-      nz = __any_sync(0xffffffffu, nz);
-      if (lane == 0) nrm2[q] = nz ? 1.0 : 0.0;
+      for (int i = 0; i < m; i += 8) {
+        real x[8];
+#pragma unroll
+        for (int rr = 0; rr < 8; rr++) x[rr] = (i + rr < m) ? arena[p + (int64_t)(i + rr) * st] : real(0);
+#pragma unroll
+        for (int rr = 0; rr < 8; rr++) nz |= (x[rr] != real(0));
+      }
+      orig[q] = nz ? 1.0 : 0.0;
     }
+    __syncthreads();
+    // exclusive scan of the flags: contiguous chunk per thread
+    const int per = (nc + blockDim.x - 1) / blockDim.x;
+    const int c0 = min(nc, (int)threadIdx.x * per), c1 = min(nc, c0 + per);
+    int cnt = 0;
+    for (int q = c0; q < c1; q++) cnt += (orig[q] != 0.0);
+    red_i[threadIdx.x] = cnt;
     __syncthreads();
     if (threadIdx.x == 0) {
-      int c = 0;
-      for (int q = 0; q < tk.ncolG; q++) {
-        double f = nrm2[q];
-        orig[q] = (f != 0.0) ? (double)c : -1.0;
-        c += (f != 0.0);
+      int acc = 0;
+      for (int t = 0; t < (int)blockDim.x; t++) {
+        int v = red_i[t];
+        red_i[t] = acc;
+        acc += v;
       }
-      s_ncol = c;
+      s_ncol = acc;
     }
     __syncthreads();
-    for (int q = warp; q < tk.ncolG; q += nwarp) {
-      int dst = (int)orig[q];
-      if (dst < 0) continue;
+    int dst = red_i[threadIdx.x];
+    for (int q = c0; q < c1; q++) orig[q] = (orig[q] != 0.0) ? (double)(dst++) : -1.0;
+    __syncthreads();
+    const int ncomp = s_ncol;
+    // copy: one thread per column; consecutive threads write consecutive
+    // entries of a row of the row-major G
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      const int d = (int)orig[q];
+      if (d < 0) continue;
       const int64_t p = gptr[tk.gcol + q];
       const int st = gstr[tk.gcol + q];
-      for (int i = lane; i < m; i += 32) W_G[i + (int64_t)dst * m] = arena[p + (int64_t)i * st];
+      for (int i = 0; i < m; i += 8) {
+        real x[8];
+#pragma unroll
+        for (int rr = 0; rr < 8; rr++) x[rr] = (i + rr < m) ? arena[p + (int64_t)(i + rr) * st] : real(0);
+#pragma unroll
+        for (int rr = 0; rr < 8; rr++)
+          if (i + rr < m) W_G[(int64_t)(i + rr) * ncomp + d] = x[rr];
+      }
     }
     __syncthreads();
   }
+  mark(2);
   const int ncol = s_ncol;
   int k = 0;
   if (ncol > 0) {
     int kmax = m;
     if (max_rank > 0) kmax = min(kmax, max_rank);
-    k = cta_householder_qr<real>(m, ncol, W_G, m, nrm2, orig, tau, true, eps, kmax,
-                                 noise_rtol * s_amax, red_d, red_i);
+    k = cta_householder_qr<real, true>(m, ncol, W_G, ncol, nrm2, orig, tau, true, eps, kmax,
+                                       noise_rtol * s_amax, red_d, red_i, vsh);
   }
   if (threadIdx.x == 0) rank[tk.s] = k;
+  mark(3);
   if (k == m) return;  // untouched: all unknowns coarse, E_s = I
   const int f = m - k;
 
-  if (k == 0) {
-    // E_s = I: T' = L^{-1} (Cholesky) or L^{-1} P (LU); T'_R^T = U^{-T}
-    if (sym) {
-      cta_tri_inv_lower<real>(m, W_A, m, false, T, m);
-    } else {
-      cta_tri_inv_lower<real>(m, W_A, m, true, W_L, m);
-      // T = L^{-1} P: column c of P is e_{perm^{-1}(c)}; apply swaps to columns
-      // (L^{-1} P)[:, c] = L^{-1}[:, pos(c)], pos(c) = row of P A that
-      // holds original row c after the swaps piv[0..m-1] in order
-      cta_copy<real>(m, m, W_L, m, W_S, m);
-      for (int c = threadIdx.x; c < m; c += blockDim.x) {
-        // position of original row c after the swaps
-        int pos = c;
-        for (int j = 0; j < m; j++) {
-          if (piv[j] == pos) pos = j;
-          else if (j == pos) pos = piv[j];
-        }
-        for (int i = 0; i < m; i++) T[i + (int64_t)c * m] = W_S[i + (int64_t)pos * m];
-      }
-      __syncthreads();
-      cta_tri_inv_upper<real>(m, W_A, m, W_L, m);
-      // T'_R^T = (U^{-1})^T
+  if (sym) {
+    // L^{-1} in place (lower), then B = L^{-T} L^{-1}
+    cta_trtri_lower<real>(m, W_A, m, false, tsh);
+    cta_zero_tri<real>(m, W_A, m, true);
+    if (k == 0) {  // E_s = I: T' = L^{-1}
+      cta_copy<real>(m, m, W_A, m, T, m);
+      return;
+    }
+    cta_gemm<real>(m, m, m, W_A, m, true, W_A, m, false, W_B, m, real(1), real(0), gsh);
+  } else {
+    // L^{-1} (unit lower) into W_L, U^{-1} into W_S
+    cta_copy<real>(m, m, W_A, m, W_L, m);
+    cta_copy<real>(m, m, W_A, m, W_S, m);
+    cta_trtri_lower<real>(m, W_L, m, true, tsh);
+    cta_zero_tri<real>(m, W_L, m, true);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) W_L[i + (int64_t)i * m] = real(1);
+    cta_trtri_upper<real>(m, W_S, m, tsh);
+    cta_zero_tri<real>(m, W_S, m, false);
+    if (k == 0) {
+      // E_s = I: T' = L^{-1} P, T'_R^T = (U^{-1})^T
+      cta_permute_cols<real>(m, piv, W_L, m, T, m);
       real* TRt = fac + tk.TR;
       for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
         int i = idx % m, j = idx / m;
-        TRt[i + (int64_t)j * m] = W_L[j + (int64_t)i * m];
+        TRt[i + (int64_t)j * m] = W_S[j + (int64_t)i * m];
       }
       __syncthreads();
-    }
-    return;
-  }
-
-  // ---- A_ss^{-1}
-  if (sym) {
-    cta_tri_inv_lower<real>(m, W_A, m, false, W_L, m);
-    cta_gemm<real>(m, m, m, W_L, m, true, W_L, m, false, W_B, m, real(1), real(0));
-  } else {
-    // B = U^{-1} L^{-1} P
-    cta_tri_inv_lower<real>(m, W_A, m, true, W_L, m);
-    cta_tri_inv_upper<real>(m, W_A, m, W_S, m);
-    cta_gemm<real>(m, m, m, W_S, m, false, W_L, m, false, W_F, m, real(1), real(0));
-    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      int pos = c;
-      for (int j = 0; j < m; j++) {
-        if (piv[j] == pos) pos = j;
-        else if (j == pos) pos = piv[j];
-      }
-      for (int i = 0; i < m; i++) W_B[i + (int64_t)c * m] = W_F[i + (int64_t)pos * m];
-    }
-    __syncthreads();
-  }
-
-  // ---- U = first k columns of Q of the pivoted QR
-  cta_form_q<real>(m, k, W_G, m, tau, 0, k, W_U, m);
-
-  // ---- V_L: complement of X = B U (full QR of X, V = Q[:, k:])
-  cta_gemm<real>(m, k, m, W_B, m, false, W_U, m, false, W_X, m, real(1), real(0));
-  cta_householder_qr<real>(m, k, W_X, m, nrm2, orig, tau2, false, 0.0, k, 0.0, red_d, red_i);
-  cta_form_q<real>(m, k, W_X, m, tau2, k, f, W_V, m);
-
-  // ---- T = [U^T B; V_L^T B]
-  cta_gemm<real>(k, m, m, W_U, m, true, W_B, m, false, W_T, m, real(1), real(0));
-  cta_gemm<real>(f, m, m, W_V, m, true, W_B, m, false, W_T + k, m, real(1), real(0));
-  // C = U^T B U (k x k) -> coarse (s,s) block
-  cta_gemm<real>(k, k, m, W_T, m, false, W_U, m, false, W_C, m, real(1), real(0));
-  real* blk_ss = arena + tk.a_ss;
-
-  if (sym) {
-    // F = V^T B V, Cholesky, T' rows k.. = L_F^{-1} V^T B
-    cta_gemm<real>(f, f, m, W_T + k, m, false, W_V, m, false, W_F, m, real(1), real(0));
-    if (!cta_cholesky<real>(f, W_F, m, &sflag)) {
-      if (threadIdx.x == 0) {
-        if (atomicCAS(&err->code, 0, (int)HSOLVE_ERR_NOT_SPD) == 0) {
-          err->cluster = tk.s;
-          err->level = level;
-        }
-        rank[tk.s] = m;
-      }
       return;
     }
-    cta_tri_inv_lower<real>(f, W_F, m, false, W_L, m);
+    // B = U^{-1} L^{-1} P
+    cta_gemm<real>(m, m, m, W_S, m, false, W_L, m, false, W_F, m, real(1), real(0), gsh);
+    cta_permute_cols<real>(m, piv, W_F, m, W_B, m);
+  }
+
+  mark(4);
+  // ---- U = first k columns of Q of the pivoted QR
+  cta_form_q<real, true>(m, k, W_G, ncol, tau, 0, k, W_U, m, vsh);
+
+  // ---- V_L: complement of X = B U (full QR of X, V = Q[:, k:]); in the SPD
+  // case X takes the (spent) shared-memory home of the factor of A_ss
+  if (sym) W_X = W_A;
+  cta_gemm<real>(m, k, m, W_B, m, false, W_U, m, false, W_X, m, real(1), real(0), gsh);
+  cta_householder_qr<real, false>(m, k, W_X, m, nrm2, orig, tau2, false, 0.0, k, 0.0, red_d,
+                                  red_i, vsh);
+  W_V = W_U + (int64_t)k * m;
+  cta_form_q<real, false>(m, k, W_X, m, tau2, k, f, W_V, m, vsh);
+
+  mark(5);
+  // ---- T = [U V_L]^T B (one product); C = U^T B U -> coarse (s,s) block
+  cta_gemm<real>(m, m, m, W_U, m, true, W_B, m, false, W_T, m, real(1), real(0), gsh);
+  cta_gemm<real>(k, k, m, W_T, m, false, W_U, m, false, W_C, m, real(1), real(0), gsh);
+
+  if (sym) {
+    // F = V^T B V; L_F^{-1}; T' rows k.. = L_F^{-1} V^T B.  F lives where the
+    // factor of A_ss was (shared memory when it fits): that factor is spent.
+    W_F = W_A;
+    mark(6);
+    cta_gemm<real>(f, f, m, W_T + k, m, false, W_V, m, false, W_F, m, real(1), real(0), gsh);
+    if (!cta_cholesky<real>(f, W_F, m, &sflag)) {
+      report<real>(err, (int)HSOLVE_ERR_NOT_SPD, tk.s, level, rank, m);
+      return;
+    }
+    cta_trtri_lower<real>(f, W_F, m, false, tsh);
+    cta_zero_tri<real>(f, W_F, m, true);
     cta_copy<real>(k, m, W_T, m, T, m);
-    cta_gemm<real>(f, m, f, W_L, m, false, W_T + k, m, false, T + k, m, real(1), real(0));
+    cta_gemm<real>(f, m, f, W_F, m, false, W_T + k, m, false, T + k, m, real(1), real(0), gsh);
     // D = C U^T (k x m) for the coarse-to-far update C (U^T A_sw)
-    cta_gemm<real>(k, m, k, W_C, m, false, W_U, m, true, ws_all + tk.D, m, real(1), real(0));
+    cta_gemm<real>(k, m, k, W_C, m, false, W_U, m, true, ws_all + tk.D, m, real(1), real(0), gsh);
   } else {
     // V_R: complement of B^T U
-    cta_gemm<real>(m, k, m, W_B, m, true, W_U, m, false, W_X, m, real(1), real(0));
-    cta_householder_qr<real>(m, k, W_X, m, nrm2, orig, tau2, false, 0.0, k, 0.0, red_d, red_i);
-    cta_form_q<real>(m, k, W_X, m, tau2, k, f, W_R, m);
+    cta_gemm<real>(m, k, m, W_B, m, true, W_U, m, false, W_X, m, real(1), real(0), gsh);
+    cta_householder_qr<real, false>(m, k, W_X, m, nrm2, orig, tau2, false, 0.0, k, 0.0, red_d,
+                                    red_i, vsh);
+    cta_form_q<real, false>(m, k, W_X, m, tau2, k, f, W_R, m, vsh);
     // F = V_L^T B V_R (f x f) and its LU
-    cta_gemm<real>(f, f, m, W_T + k, m, false, W_R, m, false, W_F, m, real(1), real(0));
-    if (!cta_lu<real>(f, W_F, m, piv, reinterpret_cast<real*>(red_d), red_i, &sflag)) {
-      if (threadIdx.x == 0) {
-        if (atomicCAS(&err->code, 0, (int)HSOLVE_ERR_SINGULAR) == 0) {
-          err->cluster = tk.s;
-          err->level = level;
-        }
-        rank[tk.s] = m;
-      }
+    cta_gemm<real>(f, f, m, W_T + k, m, false, W_R, m, false, W_F, m, real(1), real(0), gsh);
+    if (!cta_lu<real>(f, W_F, m, piv, red_d, red_i, &sflag)) {
+      report<real>(err, (int)HSOLVE_ERR_SINGULAR, tk.s, level, rank, m);
       return;
     }
     // T' rows k.. = L_F^{-1} P_F V_L^T B: permute rows of W_T[k:] by piv
     for (int j = 0; j < f; j++) {
-      int p = piv[j];
+      const int p = piv[j];
       if (p != j)
         for (int c = threadIdx.x; c < m; c += blockDim.x) {
           real t = W_T[k + j + (int64_t)c * m];
@@ -571,24 +738,30 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
         }
       __syncthreads();
     }
-    cta_tri_inv_lower<real>(f, W_F, m, true, W_L, m);
+    cta_copy<real>(f, f, W_F, m, W_L, m);
+    cta_trtri_lower<real>(f, W_L, m, true, tsh);
+    cta_zero_tri<real>(f, W_L, m, true);
+    for (int i = threadIdx.x; i < f; i += blockDim.x) W_L[i + (int64_t)i * m] = real(1);
+    __syncthreads();
     cta_copy<real>(k, m, W_T, m, T, m);
-    cta_gemm<real>(f, m, f, W_L, m, false, W_T + k, m, false, T + k, m, real(1), real(0));
+    cta_gemm<real>(f, m, f, W_L, m, false, W_T + k, m, false, T + k, m, real(1), real(0), gsh);
     // T'_R = B [U, V_R U_F^{-1}]; store its transpose
-    cta_tri_inv_upper<real>(f, W_F, m, W_L, m);
-    cta_gemm<real>(m, f, f, W_R, m, false, W_L, m, false, W_S, m, real(1), real(0));  // V_R U_F^{-1}
+    cta_trtri_upper<real>(f, W_F, m, tsh);
+    cta_zero_tri<real>(f, W_F, m, false);
+    cta_gemm<real>(m, f, f, W_R, m, false, W_F, m, false, W_S, m, real(1), real(0), gsh);
     real* TRt = fac + tk.TR;
-    // TRt rows 0..k = (B U)^T = U^T B^T ; rows k.. = (B V_R U_F^{-1})^T
-    cta_gemm<real>(k, m, m, W_U, m, true, W_B, m, true, TRt, m, real(1), real(0));
-    cta_gemm<real>(f, m, m, W_S, m, true, W_B, m, true, TRt + k, m, real(1), real(0));
-    cta_gemm<real>(k, m, k, W_C, m, false, W_U, m, true, ws_all + tk.D, m, real(1), real(0));
-    cta_gemm<real>(k, m, k, W_C, m, true, W_U, m, true, ws_all + tk.D2, m, real(1), real(0));
+    cta_gemm<real>(k, m, m, W_U, m, true, W_B, m, true, TRt, m, real(1), real(0), gsh);
+    cta_gemm<real>(f, m, m, W_S, m, true, W_B, m, true, TRt + k, m, real(1), real(0), gsh);
+    cta_gemm<real>(k, m, k, W_C, m, false, W_U, m, true, ws_all + tk.D, m, real(1), real(0), gsh);
+    cta_gemm<real>(k, m, k, W_C, m, true, W_U, m, true, ws_all + tk.D2, m, real(1), real(0), gsh);
   }
   // write C into the (s,s) block (coarse part); done last: A_ss was copied
+  real* blk_ss = arena + tk.a_ss;
   for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
     int i = idx % k, j = idx / k;
     blk_ss[i + (int64_t)j * tk.ld] = W_C[i + (int64_t)j * m];
   }
+  mark(7);
 }
 
 }  // namespace
@@ -597,16 +770,26 @@ template <typename real>
 void Launch<real>::prep(const PrepTask* tasks_dev, int ntask, real* arena, real* fac, real* ws,
                         double* wsd, const int64_t* gptr, const int* gstr, int* rank, double eps,
                         int sym, int max_rank, int maxm, DevError* err, int level,
-                        cudaStream_t st) {
-  (void)maxm;
+                        long long* dbg, cudaStream_t st) {
   if (ntask <= 0) return;
   // rounding-noise floor of the rank decision, relative to max |A_ss|: the
   // oracle's 1e-14 in float64; float32 blocks carry ~1e-7 relative noise
   const double noise_rtol = sizeof(real) == 8 ? 1e-14 : 1e-6;
+  // the factor of A_ss and A_ss^{-1} in shared memory when they fit
+  const size_t budget = 220 * 1024 - 2 * GK * (GT + 1) * sizeof(real) - 4 * 1024;
+  const size_t one = sizeof(real) * (size_t)maxm * maxm;
+  const size_t vec = sizeof(real) * 2 * (size_t)maxm;
+  int mats = 0;
+  if (3 * one + vec <= budget) mats = 3;
+  else if (2 * one + vec <= budget) mats = 2;
+  else if (one + vec <= budget) mats = 1;
+  const size_t smem = mats * one + vec;
+  cudaFuncSetAttribute(prep_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)std::max<size_t>(smem, 48 * 1024));
   count_launch();
-  prep_kernel<real><<<ntask, kPrepThreads, 0, st>>>(tasks_dev, arena, fac, ws, wsd, gptr, gstr,
-                                                     rank, eps, noise_rtol, sym, max_rank, err,
-                                                     level);
+  prep_kernel<real><<<ntask, kPrepThreads, smem, st>>>(tasks_dev, arena, fac, ws, wsd, gptr, gstr,
+                                                        rank, eps, noise_rtol, sym, max_rank, mats,
+                                                        maxm, err, level, dbg);
 }
 
 template struct Launch<double>;

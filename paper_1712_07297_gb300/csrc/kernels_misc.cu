@@ -10,9 +10,6 @@
 //              through a row/column map (clusters of a colour touch disjoint
 //              blocks, so no atomics).
 // scatter      coarse rows/columns of a processed cluster into its blocks.
-// apply_*      Alg. 2: y_s <- T' y_s, y_N -= B_L y_f (forward) and
-//              x_f -= B_R x_N, x_s <- T_R'^T x_s (backward), one colour class
-//              per launch.
 // float64 Krylov helpers: CSR SpMV, deterministic dot products, axpy forms.
 #include <algorithm>
 #include <atomic>
@@ -209,89 +206,6 @@ __global__ void copy_blocks_kernel(const CopyTask* __restrict__ tasks, const rea
   }
 }
 
-// ---- substitution sweeps (Alg. 2) ---------------------------------------
-
-template <typename real>
-__global__ void __launch_bounds__(256)
-apply_fwd_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
-                 const real* __restrict__ fac, const int64_t* __restrict__ vmap,
-                 real* __restrict__ y, int64_t ldy, int nrhs) {
-  extern __shared__ unsigned char smem_raw[];
-  real* tmp = reinterpret_cast<real*>(smem_raw);
-  const ApplyRec rc = recs[ids[blockIdx.x]];
-  const int m = rc.m, k = rc.k;
-  if (k == m) return;
-  const int f = m - k;
-  const real* T = fac + rc.T;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int r = 0; r < nrhs; r++) {
-    real* ys = y + rc.voff + (int64_t)r * ldy;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) tmp[i] = ys[i];
-    __syncthreads();
-    // y_s <- T' y_s
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      real acc = 0;
-      for (int l = 0; l < m; l++) acc += T[i + (int64_t)l * m] * tmp[l];
-      ys[i] = acc;
-      tmp[m + i] = acc;
-    }
-    __syncthreads();
-    // y_N -= B_L y_f, B_L = (rows k.. of XT)^T (general) or of Y (SPD)
-    const real* BL = fac + (rc.sym ? rc.Y : rc.XT) + k;
-    const real* yf = tmp + m + k;
-    const int64_t* vm = vmap + rc.map;
-    for (int c = warp; c < rc.nw; c += nwarp) {
-      const real* col = BL + (int64_t)c * m;
-      real acc = 0;
-      for (int i = lane; i < f; i += 32) acc += col[i] * yf[i];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) y[vm[c] + (int64_t)r * ldy] -= acc;
-    }
-    __syncthreads();
-  }
-}
-
-template <typename real>
-__global__ void __launch_bounds__(256)
-apply_bwd_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
-                 const real* __restrict__ fac, const int64_t* __restrict__ vmap,
-                 real* __restrict__ y, int64_t ldy, int nrhs) {
-  extern __shared__ unsigned char smem_raw[];
-  real* tmp = reinterpret_cast<real*>(smem_raw);
-  const ApplyRec rc = recs[ids[blockIdx.x]];
-  const int m = rc.m, k = rc.k;
-  if (k == m) return;
-  const int f = m - k;
-  const real* BR = fac + rc.Y + k;
-  const real* TRt = fac + (rc.sym ? rc.T : rc.TR);
-  const int64_t* vm = vmap + rc.map;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int r = 0; r < nrhs; r++) {
-    real* ys = y + rc.voff + (int64_t)r * ldy;
-    // gather x_N
-    real* xn = tmp + m;
-    for (int c = threadIdx.x; c < rc.nw; c += blockDim.x) xn[c] = y[vm[c] + (int64_t)r * ldy];
-    for (int i = threadIdx.x; i < k; i += blockDim.x) tmp[i] = ys[i];
-    __syncthreads();
-    // x_f = y_f - B_R x_N
-    for (int i = threadIdx.x; i < f; i += blockDim.x) {
-      real acc = ys[k + i];
-      for (int c = 0; c < rc.nw; c++) acc -= BR[i + (int64_t)c * m] * xn[c];
-      tmp[k + i] = acc;
-    }
-    __syncthreads();
-    // x_s <- T_R'^T^T x = (TRt)^T x : out[i] = sum_l TRt[l, i] x[l]
-    for (int i = warp; i < m; i += nwarp) {
-      const real* col = TRt + (int64_t)i * m;
-      real acc = 0;
-      for (int l = lane; l < m; l += 32) acc += col[l] * tmp[l];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) ys[i] = acc;
-    }
-    __syncthreads();
-  }
-}
-
 template <typename real>
 __global__ void scatter_csr_kernel(const int64_t* __restrict__ dst, const double* __restrict__ val,
                                    int64_t nnz, real* __restrict__ arena) {
@@ -479,31 +393,6 @@ void Launch<real>::copy_blocks(const CopyTask* tasks_dev, int ntask, const real*
     count_launch();
     copy_blocks_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, src, dst);
   }
-}
-
-template <typename real>
-void Launch<real>::apply_fwd(const ApplyRec* recs, const int* ids, int nids, const real* fac,
-                             const int64_t* vmap, real* y, int64_t ldy, int nrhs, int maxm,
-                             cudaStream_t st) {
-  if (nids <= 0) return;
-  size_t sm = sizeof(real) * (size_t)(2 * maxm);
-  if (sm > 48 * 1024)
-    cudaFuncSetAttribute(apply_fwd_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  count_launch();
-  apply_fwd_kernel<real><<<nids, 256, sm, st>>>(recs, ids, fac, vmap, y, ldy, nrhs);
-}
-
-template <typename real>
-void Launch<real>::apply_bwd(const ApplyRec* recs, const int* ids, int nids, const real* fac,
-                             const int64_t* vmap, real* y, int64_t ldy, int nrhs, int maxm,
-                             cudaStream_t st) {
-  if (nids <= 0) return;
-  // maxm here is the larger of m and nw over the class
-  size_t sm = sizeof(real) * (size_t)(2 * maxm);
-  if (sm > 48 * 1024)
-    cudaFuncSetAttribute(apply_bwd_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  count_launch();
-  apply_bwd_kernel<real><<<nids, 256, sm, st>>>(recs, ids, fac, vmap, y, ldy, nrhs);
 }
 
 template <typename real>

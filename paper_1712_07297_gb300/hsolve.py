@@ -240,8 +240,9 @@ class Solver:
         _check(load().hsolve_get_perm(self.h, p.ctypes.data), self.h)
         return p
 
-    def set_profiling(self, on: bool):
-        _check(load().hsolve_set_profiling(self.h, int(bool(on))), self.h)
+    def set_profiling(self, on, per_level=False):
+        v = 0 if not on else (2 if per_level else 1)
+        _check(load().hsolve_set_profiling(self.h, v), self.h)
 
     def phase_times(self) -> dict:
         lib = load()
