@@ -139,6 +139,32 @@ hsolve_status hsolve_factor(hsolve_handle* h, double eps, hsolve_precision prec)
 hsolve_status hsolve_apply(hsolve_handle* h, const double* rhs, double* out,
                            int nrhs, int64_t ld);
 
+/* Bytes of the fixed device scratch behind hsolve_apply_noalloc. */
+#define HSOLVE_NOALLOC_SCRATCH_BYTES 33554432
+
+/* The same out = M^{-1} rhs as hsolve_apply, for callers that cannot let the
+ * library allocate device memory: no cudaMalloc, cudaFree or other
+ * allocating call is made.  (The paper has no counterpart; this is a service
+ * of the library.)  Callers this is for: code whose device memory belongs to
+ * another allocator (a framework's caching allocator, a pre-reserved pool)
+ * and code that must not incur the device synchronisation cudaMalloc and
+ * cudaFree can imply.  The factorization made by hsolve_factor is an input;
+ * every temporary vector of the sweeps comes from one file-scope device
+ * array of HSOLVE_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the
+ * library holds until the process exits.
+ * - The first call on a device looks up that array's device address (with
+ *   the device current) and caches it; make that first call before any
+ *   stream capture.
+ * - All calls share the array and it keeps the last call's contents; calls
+ *   whose device work overlaps in time (other streams, other handles) race
+ *   on it, so serialise them.
+ * - A factorization and nrhs needing more scratch than the array holds are
+ *   rejected with HSOLVE_ERR_BUDGET (hsolve_last_error gives both sizes).
+ * Other errors as hsolve_apply.  rhs and out are device pointers
+ * (column-major n x nrhs, leading dimension ld). */
+hsolve_status hsolve_apply_noalloc(hsolve_handle* h, const double* rhs, double* out,
+                                   int nrhs, int64_t ld);
+
 /* Krylov solve of A x = b with the factorization as preconditioner (Sec. 5:
  * CG for SPD matrices, right-preconditioned flexible GMRES otherwise), in
  * float64, starting from x = 0, until ||b - A x|| <= tol ||b|| for every

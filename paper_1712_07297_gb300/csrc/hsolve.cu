@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -862,6 +863,125 @@ void apply_any(hsolve_handle* h, const double* rhs, double* out, int nrhs, int64
 }
 
 // ---------------------------------------------------------------------------
+// Substitution with a fixed, library-owned scratch (hsolve_apply_noalloc)
+// ---------------------------------------------------------------------------
+// Some callers cannot let this library call cudaMalloc: their device memory
+// is owned by another allocator (a framework's caching allocator or a
+// pre-reserved pool that leaves nothing outside it), or they must not pay
+// the implicit device synchronisation that cudaMalloc/cudaFree can bring.
+// For them the substitution sweeps take every temporary vector from this
+// fixed array instead of the handle's lazily allocated buffers.  It is a
+// file-scope device array, so every GPU that loads the library holds it
+// until the process exits.  All calls share it: calls whose device work
+// overlaps (on different streams, or from different handles) race on it.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Host code cannot use g_noalloc_scratch's name as a device address (it is a
+// host-side stand-in); its device address is looked up once per device,
+// with that device current, and cached here.
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+hsolve_status noalloc_scratch_address(void** out, std::string* why) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    *why = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    return HSOLVE_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    *why = "device index beyond the scratch table";
+    return HSOLVE_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      *why = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return HSOLVE_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return HSOLVE_OK;
+}
+
+// Scratch layout per level: level vector, scratch vector, partial sums,
+// each nrhs wide and 256-byte aligned.  Returns the bytes needed.
+template <typename real>
+size_t noalloc_layout(const hsolve_handle* h, int nrhs, std::vector<size_t>* offs) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = (o + bytes + 255) / 256 * 256;
+    return at;
+  };
+  for (auto& F : h->F) {
+    const size_t nv = sizeof(real) * (size_t)std::max<int64_t>(F->P.voff[F->P.nclu], 1) * nrhs;
+    const size_t np = sizeof(real) * (size_t)std::max<int64_t>(F->part_elems, 1) * nrhs;
+    size_t a = take(nv), b = take(nv), c = take(np);
+    if (offs) {
+      offs->push_back(a);
+      offs->push_back(b);
+      offs->push_back(c);
+    }
+  }
+  return o;
+}
+
+// Same sweeps as apply_impl, with every temporary taken from `base`.  No
+// element of the scratch needs to start at zero: each one the sweeps read is
+// written earlier in the same call (perm_in fills level 0, the gathers fill
+// every coarser level, the partial sums are written before they are summed).
+template <typename real>
+void apply_scratch_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int64_t ld,
+                        unsigned char* base) {
+  std::vector<size_t> offs;
+  noalloc_layout<real>(h, nrhs, &offs);
+  const int L = (int)h->F.size();
+  auto vec = [&](int l) { return reinterpret_cast<real*>(base + offs[3 * l]); };
+  auto zv = [&](int l) { return reinterpret_cast<real*>(base + offs[3 * l + 1]); };
+  auto pt = [&](int l) { return reinterpret_cast<real*>(base + offs[3 * l + 2]); };
+  FLevel& F0 = *h->F[0];
+  const int64_t n0 = F0.P.voff[F0.P.nclu];
+  Launch<real>::perm_in(h->d_perm.as<int64_t>(), h->n, rhs, ld, vec(0), n0, nrhs, h->st);
+  for (int l = 0; l < L; l++) {
+    FLevel& F = *h->F[l];
+    const int64_t nl = std::max<int64_t>(F.P.voff[F.P.nclu], 1);
+    for (size_t c = 0; c < F.cls.size(); c++)
+      Launch<real>::apply_fwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
+                              (int)F.cls[c].size(), F.cls_maxm[c], F.cls_maxnw[c],
+                              F.fac.as<real>(), F.vmap.as<int64_t>(), vec(l), zv(l), nl, nrhs,
+                              h->st);
+    if (l + 1 < L) {
+      FLevel& G = *h->F[l + 1];
+      const int64_t ng = std::max<int64_t>(G.P.voff[G.P.nclu], 1);
+      Launch<real>::gather_vec(F.next_idx.as<int64_t>(), F.next_n, vec(l), nl, vec(l + 1), ng,
+                               nrhs, h->st);
+    }
+  }
+  for (int l = L - 1; l >= 0; l--) {
+    FLevel& F = *h->F[l];
+    const int64_t nl = std::max<int64_t>(F.P.voff[F.P.nclu], 1);
+    if (l + 1 < L) {
+      FLevel& G = *h->F[l + 1];
+      const int64_t ng = std::max<int64_t>(G.P.voff[G.P.nclu], 1);
+      Launch<real>::scatter_vec(F.next_idx.as<int64_t>(), F.next_n, vec(l + 1), ng, vec(l), nl,
+                                nrhs, h->st);
+    }
+    for (int c = (int)F.cls.size() - 1; c >= 0; c--)
+      Launch<real>::apply_bwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
+                              (int)F.cls[c].size(), F.cls_maxm[c], F.cls_maxnw[c],
+                              F.fac.as<real>(), F.vmap.as<int64_t>(), vec(l), zv(l), pt(l), nl,
+                              nrhs, h->st);
+  }
+  Launch<real>::perm_out(h->d_perm.as<int64_t>(), h->n, vec(0), n0, out, ld, nrhs, h->st);
+}
+
+// ---------------------------------------------------------------------------
 // Krylov solvers (float64)
 // ---------------------------------------------------------------------------
 struct Scalars {  // device scratch for dot products
@@ -1255,6 +1375,37 @@ hsolve_status hsolve_apply(hsolve_handle* h, const double* rhs, double* out, int
   if (!rhs || !out || nrhs < 1 || ld < h->n) return set_err(h, HSOLVE_ERR_ARG, "bad apply args");
   try {
     apply_any(h, rhs, out, nrhs, ld);
+    HS_CUDA(cudaGetLastError());
+    HS_CUDA(cudaStreamSynchronize(h->st));
+  } catch (const Fail& f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return HSOLVE_OK;
+}
+
+hsolve_status hsolve_apply_noalloc(hsolve_handle* h, const double* rhs, double* out, int nrhs,
+                                   int64_t ld) {
+  if (!h) return HSOLVE_ERR_ARG;
+  cudaGetLastError();  // a stale error of another runtime user is not ours
+  if (!h->factored) return set_err(h, HSOLVE_ERR_STATE, "apply before factor");
+  if (!rhs || !out || nrhs < 1 || ld < h->n) return set_err(h, HSOLVE_ERR_ARG, "bad apply args");
+  const size_t need = h->prec == HSOLVE_FP64 ? noalloc_layout<double>(h, nrhs, nullptr)
+                                             : noalloc_layout<float>(h, nrhs, nullptr);
+  if (need > kNoAllocScratchBytes)
+    return set_err(h, HSOLVE_ERR_BUDGET,
+                   "hsolve_apply_noalloc needs " + std::to_string(need) +
+                       " bytes of scratch for this factorization and nrhs; the fixed scratch "
+                       "holds " + std::to_string(kNoAllocScratchBytes) +
+                       " bytes (use fewer right-hand sides per call, or hsolve_apply)");
+  void* base = nullptr;
+  std::string why;
+  hsolve_status st = noalloc_scratch_address(&base, &why);
+  if (st != HSOLVE_OK) return set_err(h, st, why);
+  try {
+    if (h->prec == HSOLVE_FP64)
+      apply_scratch_impl<double>(h, rhs, out, nrhs, ld, static_cast<unsigned char*>(base));
+    else
+      apply_scratch_impl<float>(h, rhs, out, nrhs, ld, static_cast<unsigned char*>(base));
     HS_CUDA(cudaGetLastError());
     HS_CUDA(cudaStreamSynchronize(h->st));
   } catch (const Fail& f) {

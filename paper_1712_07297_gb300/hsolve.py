@@ -65,6 +65,7 @@ EXPORTS = {
                                  C.POINTER(C.c_void_p)]),
     "hsolve_factor": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "hsolve_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int64]),
+    "hsolve_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int64]),
     "hsolve_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                C.c_int, C.c_int64, C.POINTER(SolveInfo)]),
     "hsolve_solve_host": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p,
@@ -183,6 +184,17 @@ class Solver:
         if onrhs != nrhs or old != ld:
             raise ValueError("rhs/out layouts differ")
         _check(load().hsolve_apply(self.h, ptr, optr, nrhs, ld), self.h)
+        return out
+
+    def apply_noalloc(self, rhs, out):
+        """out = M^{-1} rhs through hsolve_apply_noalloc: the library
+        allocates no device memory (temporaries come from its fixed scratch
+        array); `out` must be given."""
+        ptr, nrhs, ld = _dev_ptr(rhs, self.n)
+        optr, onrhs, old = _dev_ptr(out, self.n)
+        if onrhs != nrhs or old != ld:
+            raise ValueError("rhs/out layouts differ")
+        _check(load().hsolve_apply_noalloc(self.h, ptr, optr, nrhs, ld), self.h)
         return out
 
     def spmv(self, x, y=None):
