@@ -74,6 +74,10 @@ typedef struct {
   int32_t max_rank;       /* > 0: cap every compression rank at this value
                              (the fixed-rank option of Sec. 5.1); 0 = none */
   int32_t gmres_restart;  /* GMRES restart length; default 50 */
+  int32_t compress;       /* 0 = pivoted QR of the fill block itself (Eq. lra);
+                             1 = randomized: when the fill block has more than
+                             m + 8 columns, pivoted QR of its sketch G Omega
+                             (m x (m + 8), Rademacher Omega); default 0 */
 } hsolve_opts;
 
 typedef struct {

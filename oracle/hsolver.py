@@ -32,10 +32,24 @@ Readings of points the paper leaves open (each is also listed in the design doc):
     diagonal block is zero in exact arithmetic; without this floor its
     "rank" is decided by rounding noise), or when the remaining columns are
     all exactly zero.  k = number of kept steps, U = first k columns of Q.
+  * Randomized variant (north_star's "randomized rank-revealing QR"): when
+    G has more than m + 8 columns, the same truncated pivoted QR runs on the
+    sketch G Omega with Omega[q, j] = +-1/sqrt(m + 8), signs from the top
+    bit of splitmix64((q << 32) | j), q the gathered column position.  With
+    m + 8 >= m columns the sketch spans the column space of G exactly (with
+    probability one), so eps = 0 stays a direct solver.
   * k = 0 (no fill): E_s = I and the step is one block-Cholesky/LU step
     (Sec. 2.2).  k = m: the cluster is left untouched (E_s = I, all coarse).
   * Householder convention: v = x - beta e1, beta = -sign(x_0) ||x||
-    (sign(0) = +1), H = I - 2 v v^T / v^T v.
+    (sign(0) = +1), H = I - 2 v v^T / v^T v.  The compression basis U is
+    then oriented so that R has a positive diagonal (column j of Q times
+    sign(beta_j)), i.e. U's columns are the Gram-Schmidt directions of the
+    pivot columns.  The sign of beta follows the sign of x_0, which rounding
+    decides when x_0 is near zero; with this orientation the coarse bases,
+    and every coarse block built from them, are continuous functions of the
+    data (the randomized variant below depends on those signs).
+    The complement V keeps the plain Householder columns: its basis only
+    touches the eliminated fine unknowns.
   * General (nonsymmetric) matrices: one joint basis U for the row and column
     fill; V_L is the complement of A_ss^{-1} U and V_R that of A_ss^{-T} U, so
     that the coarse/fine (s,s) coupling vanishes on both sides; the fine block
@@ -135,6 +149,33 @@ def greedy_colour(adj, d2):
 
 
 # ---------------------------------------------------------------------------
+# Sketch for the randomized variant of Eq. lra
+# ---------------------------------------------------------------------------
+
+SKETCH_OVERSAMPLE = 8
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x):
+    """SplitMix64 output function (Steele, Lea, Flood 2014; Vigna's public
+    domain reference): one 64-bit output per 64-bit input, uint64 arrays."""
+    with np.errstate(over="ignore"):
+        z = (np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        return z ^ (z >> np.uint64(31))
+
+
+def sketch_matrix(c: int, l: int) -> np.ndarray:
+    """Rademacher test matrix Omega (c x l): Omega[q, j] = +-1/sqrt(l), the
+    sign being the top bit of splitmix64((q << 32) | j)."""
+    q = np.arange(c, dtype=np.uint64)[:, None]
+    j = np.arange(l, dtype=np.uint64)[None, :]
+    z = splitmix64((q << np.uint64(32)) | j)
+    return (1.0 - 2.0 * (z >> np.uint64(63)).astype(np.float64)) / np.sqrt(l)
+
+
+# ---------------------------------------------------------------------------
 # Householder pieces (shared convention, see module docstring)
 # ---------------------------------------------------------------------------
 
@@ -163,7 +204,7 @@ def cpqr(G: np.ndarray, eps: float, max_rank: int | None = None, floor: float = 
     m, c = G.shape
     A = np.array(G, dtype=np.float64, copy=True)
     cols = np.arange(c)
-    vs, taus, piv, rdiag = [], [], [], []
+    vs, taus, piv, rdiag, signs = [], [], [], [], []
     r11 = None
     k = 0
     margin = np.inf
@@ -195,15 +236,18 @@ def cpqr(G: np.ndarray, eps: float, max_rank: int | None = None, floor: float = 
         A[j:, j:] -= tau * np.outer(v, v @ A[j:, j:])
         vs.append(v)
         taus.append(tau)
+        signs.append(-1.0 if beta < 0 else 1.0)
         piv.append(int(cols[j]))
         rdiag.append(float(r))
         k = j + 1
-    # U = H_0 ... H_{k-1} [I_k; 0]
+    # U = H_0 ... H_{k-1} [I_k; 0], each column j then signed like beta_j so
+    # that R has a positive diagonal (see the module docstring)
     U = np.zeros((m, k))
     U[:k, :k] = np.eye(k)
     for j in range(k - 1, -1, -1):
         v, tau = vs[j], taus[j]
         U[j:, :] -= tau * np.outer(v, v @ U[j:, :])
+    U *= np.array(signs[:k]) if k else 1.0
     return dict(k=k, U=U, piv=piv, rdiag=rdiag, margin=margin)
 
 
@@ -313,7 +357,7 @@ def _dense_top(blocks, sizes, symmetric):
     return dict(n=n, kind="lu", P=P, L=L, U=U)
 
 
-def _process_cluster(s, blocks, cur, adj, d2, eps, symmetric, max_rank):
+def _process_cluster(s, blocks, cur, adj, d2, eps, symmetric, max_rank, compress=0):
     m = cur[s]
     N = sorted(j for j in adj[s] if cur[j] > 0)
     W = sorted(j for j in d2[s] if cur[j] > 0 and (s, j) in blocks)
@@ -323,11 +367,19 @@ def _process_cluster(s, blocks, cur, adj, d2, eps, symmetric, max_rank):
     if not symmetric:
         parts += [blocks[(w, s)][:cur[w], :m].T for w in W]
     G = np.hstack(parts) if parts else np.zeros((m, 0))
-    G = G[:, np.any(G != 0.0, axis=0)]
-    if G.shape[1] == 0:
-        cp = dict(k=0, U=np.zeros((m, 0)), piv=[], rdiag=[], margin=np.inf)
+    floor = NOISE_FLOOR * np.abs(Ass).max()
+    l = m + SKETCH_OVERSAMPLE
+    if compress == 1 and G.shape[1] > l:
+        # randomized variant: the same pivoted QR on the sketch G Omega,
+        # Omega indexed by the gathered column position (zero columns too)
+        cp = cpqr(G @ sketch_matrix(G.shape[1], l), eps, max_rank, floor=floor)
+        G = G[:, np.any(G != 0.0, axis=0)]
     else:
-        cp = cpqr(G, eps, max_rank, floor=NOISE_FLOOR * np.abs(Ass).max())
+        G = G[:, np.any(G != 0.0, axis=0)]
+        if G.shape[1] == 0:
+            cp = dict(k=0, U=np.zeros((m, 0)), piv=[], rdiag=[], margin=np.inf)
+        else:
+            cp = cpqr(G, eps, max_rank, floor=floor)
     k = cp["k"]
     widths = [(n, cur[n]) for n in N]
     AsN = np.hstack([blocks[(s, n)][:m, :w] for n, w in widths]) if N else np.zeros((m, 0))
@@ -397,8 +449,14 @@ def _process_cluster(s, blocks, cur, adj, d2, eps, symmetric, max_rank):
 
 
 def factor(prob_rowptr, prob_col, prob_val, coords, leaf: int, eps: float,
-           symmetric: bool = True, top_size: int = 0, max_rank: int | None = None):
-    """Hierarchical_Factor (Alg. 1) on a CSR matrix.  Returns a Factorization."""
+           symmetric: bool = True, top_size: int = 0, max_rank: int | None = None,
+           compress: int = 0):
+    """Hierarchical_Factor (Alg. 1) on a CSR matrix.  Returns a Factorization.
+
+    compress = 0: pivoted QR of the fill block G itself (Eq. lra);
+    compress = 1: when G has more than m + 8 columns, pivoted QR of the
+    sketch G Omega (m x (m + 8), Rademacher Omega from `sketch_matrix`)
+    instead -- the randomized rank-revealing variant."""
     depth, leaves = rcb_leaves(np.asarray(coords, dtype=np.float64), leaf)
     perm = np.concatenate(leaves).astype(np.int64)
     sizes, pairs, blocks = _level0_blocks(prob_rowptr, prob_col, prob_val, leaves)
@@ -427,7 +485,7 @@ def factor(prob_rowptr, prob_col, prob_val, coords, leaf: int, eps: float,
         for s in order:
             if cur[s] == 0:
                 continue
-            cf = _process_cluster(s, blocks, cur, adj, d2, eps, symmetric, max_rank)
+            cf = _process_cluster(s, blocks, cur, adj, d2, eps, symmetric, max_rank, compress)
             facs[s] = cf
             cur[s] = cf.k
         levels.append(Level(nclu, sizes, offsets, adj, d2, colour, order, facs, cur.copy()))

@@ -74,6 +74,17 @@ struct PrepTask {
   int64_t TR;       // factor offset of T'_R (general only)
   int64_t D;        // workspace offset of D = C U^T (k x m, ld m)
   int64_t D2;       // workspace offset of D2 = C^T U^T (general only)
+  int l;            // > 0: pivoted QR of the sketch Y (m x l) instead of G
+  int pad;
+  int64_t Y;        // workspace offset of the sketch Y (ld m)
+};
+
+// Sketch task: Y (m x l, ld m) = G Omega for the gathered fill columns of
+// one cluster, Omega[q, j] = +-1/sqrt(l) (splitmix64 sign of (q << 32) | j).
+struct SketchTask {
+  int m, l, ncol, pad;
+  int64_t gcol;     // offset into the column-descriptor arrays
+  int64_t Y;        // workspace offset of Y
 };
 
 // Grouped GEMM task: C (M x N, ldc) = A (M x K, lda) * Bg, where column j of
@@ -134,6 +145,9 @@ struct Launch {
                    real* ws, double* wsd, const int64_t* gptr, const int* gstr,
                    int* rank, double eps, int sym, int max_rank, int maxm,
                    DevError* err, int level, long long* dbg, cudaStream_t st);
+  static void sketch(const SketchTask* tasks_dev, int ntask, int maxm, int maxl,
+                     const real* arena, real* ws, const int64_t* gptr, const int* gstr,
+                     cudaStream_t st);
   static void gemm_gather(const GemmTask* tasks_dev, int ntask, int maxM, int maxN,
                           const real* Abase, real* Cbase, const real* Bbase,
                           const int64_t* bptr, const int* bstr, const int* rank,

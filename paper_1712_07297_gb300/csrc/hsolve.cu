@@ -24,6 +24,8 @@ using namespace hs;
 
 namespace {
 
+constexpr int kSketchOversample = 8;  // sketch width m + 8 (randomized Eq. lra)
+
 // ---------------------------------------------------------------------------
 // Small helpers
 // ---------------------------------------------------------------------------
@@ -349,6 +351,8 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     FL.cls.push_back(S);
     const int nt = (int)S.size();
     std::vector<PrepTask> prep(nt);
+    std::vector<SketchTask> sk;
+    int maxl = 0;
     std::vector<GemmTask> gY, gXT, gE, gE2;
     std::vector<SchurTask> sch;
     std::vector<ScatterSeg> segN, segW;
@@ -428,8 +432,25 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       int64_t E2off = ws_e;
       if (!sym) ws_e += (int64_t)m * std::max(nwf, 1);
       ws_e = (ws_e + 3) / 4 * 4;
+      // randomized compression: sketch Y = G Omega when G is wider than m + 8
+      pt.l = 0;
+      pt.Y = 0;
+      if (h->opts.compress == 1 && ncolG > m + kSketchOversample) {
+        pt.l = m + kSketchOversample;
+        pt.Y = ws_e;
+        ws_e += (int64_t)m * pt.l;
+        ws_e = (ws_e + 3) / 4 * 4;
+        SketchTask t{};
+        t.m = m;
+        t.l = pt.l;
+        t.ncol = ncolG;
+        t.gcol = gcol;
+        t.Y = pt.Y;
+        sk.push_back(t);
+        maxl = std::max(maxl, pt.l);
+      }
       pt.wsd = wsd_e;
-      wsd_e += 2 * (int64_t)ncolG + 3 * m + 8;
+      wsd_e += 2 * (int64_t)std::max(ncolG, m + kSketchOversample) + 4 * m + 8;
       pt.T = oT[s];
       pt.TR = sym ? oT[s] : oTR[s];
       // Y = T' A_sN  (rows 0..k coarse rows, rows k.. = B_R)
@@ -511,6 +532,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     }
     // ---- upload this class's task arrays
     Blob b;
+    size_t o_sk = b.add(sk);
     size_t o_prep = b.add(prep), o_gY = b.add(gY), o_gXT = b.add(gXT), o_gE = b.add(gE),
            o_gE2 = b.add(gE2), o_sch = b.add(sch), o_segN = b.add(segN), o_segW = b.add(segW),
            o_gptr = b.add(gptr), o_gstr = b.add(gstr), o_smap = b.add(smap),
@@ -521,6 +543,11 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     real* ws = h->ws.as<real>();
     const int64_t* d_gptr = reinterpret_cast<const int64_t*>(d + o_gptr);
     const int* d_gstr = reinterpret_cast<const int*>(d + o_gstr);
+    if (!sk.empty())
+      timed_lv(h, "sketch", level, 1, [&] {
+        Launch<real>::sketch(reinterpret_cast<const SketchTask*>(d + o_sk), (int)sk.size(), maxm,
+                             maxl, arena, ws, d_gptr, d_gstr, h->st);
+      });
     long long* dbg = nullptr;
     if (h->profiling && h->profile_levels) {
       h->dbg.ensure(sizeof(long long) * 8 * (size_t)nt);
@@ -1226,6 +1253,7 @@ void hsolve_default_opts(hsolve_opts* o) {
   o->top_size = 0;
   o->max_rank = 0;
   o->gmres_restart = 50;
+  o->compress = 0;
 }
 
 hsolve_status hsolve_analyze(const hsolve_csr* A, const double* coords, int dim,

@@ -303,7 +303,7 @@ __device__ double cta_sum_d(double v, double* red) {
 template <typename real, bool RowMajor>
 __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, double* orig,
                                   real* tau, bool pivot, double eps, int kmax, double floor,
-                                  double* red_d, int* red_i, real* vsh) {
+                                  double* red_d, int* red_i, real* vsh, real* rsign = nullptr) {
   auto at = [&](int i, int q) -> real& {
     return RowMajor ? G[(int64_t)i * ldg + q] : G[i + (int64_t)q * ldg];
   };
@@ -380,6 +380,7 @@ __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, 
     if (threadIdx.x == 0) {
       at(j, j) = (real)(x0 - beta);
       tau[j] = (real)tj;
+      if (rsign) rsign[j] = beta < 0.0 ? real(-1) : real(1);
     }
     const real rt = (real)tj;
     // apply to the remaining columns, CB columns per thread and RB rows per
@@ -556,7 +557,8 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
   double* orig = nrm2 + tk.ncolG;
   real* tau = reinterpret_cast<real*>(orig + tk.ncolG);
   real* tau2 = tau + m;
-  int* piv = reinterpret_cast<int*>(tau2 + m);
+  real* rsign = tau2 + m;  // sign of R's diagonal in the pivoted QR
+  int* piv = reinterpret_cast<int*>(rsign + m);
   real* T = fac + tk.T;
 
   // ---- A_ss, its largest magnitude (scale of the noise floor), its factor
@@ -576,8 +578,10 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
   }
 
   mark(1);
+  const bool sketched = tk.l > 0;
   // ---- gather the nonzero fill columns into G (Eq. lra input), row-major
-  {
+  // (not needed when the pivoted QR runs on the sketch Y = G Omega)
+  if (!sketched) {
     const int nc = tk.ncolG;
     // flag nonzero columns: one thread per column, batched independent loads
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
@@ -634,13 +638,23 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
     __syncthreads();
   }
   mark(2);
-  const int ncol = s_ncol;
+  const int ncol = sketched ? tk.l : s_ncol;
   int k = 0;
-  if (ncol > 0) {
-    int kmax = m;
-    if (max_rank > 0) kmax = min(kmax, max_rank);
+  int kmax = m;
+  if (max_rank > 0) kmax = min(kmax, max_rank);
+  if (sketched) {
+    // pivoted QR of the sketch (column-major m x l), in the shared memory of
+    // the not yet used A_ss^{-1} and [U V] buffers when it fits; the kept
+    // reflectors then move to W_G (column-major, ld m) for U
+    real* Ysrc = ws_all + tk.Y;
+    real* Yq = (smem_mats >= 3 && (int64_t)m * tk.l <= 2 * (int64_t)smem_m * smem_m) ? W_B : Ysrc;
+    if (Yq != Ysrc) cta_copy<real>(m, tk.l, Ysrc, m, Yq, m);
+    k = cta_householder_qr<real, false>(m, tk.l, Yq, m, nrm2, orig, tau, true, eps, kmax,
+                                        noise_rtol * s_amax, red_d, red_i, vsh, rsign);
+    cta_copy<real>(m, k, Yq, m, W_G, m);
+  } else if (ncol > 0) {
     k = cta_householder_qr<real, true>(m, ncol, W_G, ncol, nrm2, orig, tau, true, eps, kmax,
-                                       noise_rtol * s_amax, red_d, red_i, vsh);
+                                       noise_rtol * s_amax, red_d, red_i, vsh, rsign);
   }
   if (threadIdx.x == 0) rank[tk.s] = k;
   mark(3);
@@ -683,7 +697,16 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
 
   mark(4);
   // ---- U = first k columns of Q of the pivoted QR
-  cta_form_q<real, true>(m, k, W_G, ncol, tau, 0, k, W_U, m, vsh);
+  if (sketched)
+    cta_form_q<real, false>(m, k, W_G, m, tau, 0, k, W_U, m, vsh);
+  else
+    cta_form_q<real, true>(m, k, W_G, ncol, tau, 0, k, W_U, m, vsh);
+  // orient U so that R has a positive diagonal (Gram-Schmidt directions)
+  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x) {
+    int i = idx % m, j = idx / m;
+    W_U[i + (int64_t)j * m] *= rsign[j];
+  }
+  __syncthreads();
 
   // ---- V_L: complement of X = B U (full QR of X, V = Q[:, k:]); in the SPD
   // case X takes the (spent) shared-memory home of the factor of A_ss

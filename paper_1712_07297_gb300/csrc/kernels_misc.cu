@@ -102,6 +102,81 @@ gemm_gather_kernel(const GemmTask* __restrict__ tasks, const real* __restrict__ 
     }
 }
 
+// SplitMix64 output function (Steele, Lea, Flood 2014; Vigna's public
+// domain reference implementation).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Y (m x l) = G Omega: G's columns gathered through descriptors, Omega
+// generated on the fly (Rademacher, +-1/sqrt(l)); the randomized variant of
+// the compression of Eq. lra.  64 x 64 output tiles, inner chunks of 16
+// gathered columns.
+template <typename real>
+__global__ void __launch_bounds__(256)
+sketch_kernel(const SketchTask* __restrict__ tasks, const real* __restrict__ arena,
+              real* __restrict__ ws, const int64_t* __restrict__ gptr,
+              const int* __restrict__ gstr) {
+  const SketchTask tk = tasks[blockIdx.z];
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+  if (i0 >= tk.m || j0 >= tk.l) return;
+  __shared__ real As[TK][TM + 1];
+  __shared__ real Bs[TK][TN + 1];
+  const real scale = real(1) / sqrt((real)tk.l);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  real acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) acc[a][b] = 0;
+  for (int q0 = 0; q0 < tk.ncol; q0 += TK) {
+    for (int e = threadIdx.x; e < TM * TK; e += 256) {
+      int i = e % TM, l = e / TM;
+      int gi = i0 + i, q = q0 + l;
+      real v = 0;
+      if (gi < tk.m && q < tk.ncol)
+        v = arena[gptr[tk.gcol + q] + (int64_t)gi * gstr[tk.gcol + q]];
+      As[l][i] = v;
+    }
+    for (int e = threadIdx.x; e < TK * TN; e += 256) {
+      int l = e % TK, j = e / TK;
+      int q = q0 + l, gj = j0 + j;
+      real v = 0;
+      if (q < tk.ncol && gj < tk.l) {
+        uint64_t z = splitmix64(((uint64_t)q << 32) | (uint64_t)gj);
+        v = (z >> 63) ? -scale : scale;
+      }
+      Bs[l][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < TK; l++) {
+      real a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        a[q] = As[l][ty + 16 * q];
+        b[q] = Bs[l][tx + 16 * q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[p][q] += a[p] * b[q];
+    }
+    __syncthreads();
+  }
+  real* Y = ws + tk.Y;
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int gi = i0 + ty + 16 * p, gj = j0 + tx + 16 * q;
+      if (gi < tk.m && gj < tk.l) Y[gi + (int64_t)gj * tk.m] = acc[p][q];
+    }
+}
+
 // C_mapped[r, c] -= sum_i P[k+i, r] Q[k+i, c], i < f = m - rank.
 template <typename real>
 __global__ void __launch_bounds__(256)
@@ -358,6 +433,18 @@ void Launch<real>::gemm_gather(const GemmTask* tasks_dev, int ntask, int maxM, i
     count_launch();
     gemm_gather_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, Abase, Cbase, Bbase, bptr,
                                                     bstr, rank);
+  }
+}
+
+template <typename real>
+void Launch<real>::sketch(const SketchTask* tasks_dev, int ntask, int maxm, int maxl,
+                          const real* arena, real* ws, const int64_t* gptr, const int* gstr,
+                          cudaStream_t st) {
+  if (ntask <= 0 || maxm <= 0 || maxl <= 0) return;
+  for (int t0 = 0; t0 < ntask; t0 += kMaxGridYZ) {
+    dim3 grid((maxl + TN - 1) / TN, (maxm + TM - 1) / TM, std::min(kMaxGridYZ, ntask - t0));
+    count_launch();
+    sketch_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, arena, ws, gptr, gstr);
   }
 }
 

@@ -37,7 +37,7 @@ class Csr(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("symmetric", C.c_int32), ("top_size", C.c_int64),
-                ("max_rank", C.c_int32), ("gmres_restart", C.c_int32)]
+                ("max_rank", C.c_int32), ("gmres_restart", C.c_int32), ("compress", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -133,7 +133,7 @@ class Solver:
     """One analysed matrix: analyze -> factor -> apply / solve."""
 
     def __init__(self, rowptr, col, val, coords=None, *, leaf_size=128, symmetric=-1, top_size=0,
-                 max_rank=0, gmres_restart=50, stream=None):
+                 max_rank=0, gmres_restart=50, compress=0, stream=None):
         lib = load()
         self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         self.col = np.ascontiguousarray(col, dtype=np.int32)
@@ -143,7 +143,7 @@ class Solver:
                   self.val.ctypes.data)
         o = default_opts()
         o.leaf_size, o.symmetric, o.top_size = leaf_size, symmetric, top_size
-        o.max_rank, o.gmres_restart = max_rank, gmres_restart
+        o.max_rank, o.gmres_restart, o.compress = max_rank, gmres_restart, compress
         h = C.c_void_p()
         cptr, dim = None, 0
         if coords is not None:

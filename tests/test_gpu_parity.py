@@ -31,9 +31,9 @@ def hs():
     return hsolve
 
 
-def _oracle(p, leaf, eps, top_size=0, max_rank=None):
+def _oracle(p, leaf, eps, top_size=0, max_rank=None, compress=0):
     return H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=p.symmetric,
-                    top_size=top_size, max_rank=max_rank)
+                    top_size=top_size, max_rank=max_rank, compress=compress)
 
 
 def _rel(a, b):
@@ -126,6 +126,27 @@ def test_general_matches_oracle(hs, mk, leaf, eps):
     xx = x.cpu().numpy()
     for c in range(2):
         assert np.linalg.norm(b[c] - A @ xx[c]) <= 1.0001e-10 * np.linalg.norm(b[c])
+    s.close()
+
+
+@pytest.mark.parametrize("name,mk,leaf,eps", [
+    ("poisson2d_64", lambda: I.poisson((64, 64)), 64, 1e-3),
+    ("poisson3d_16", lambda: I.poisson((16, 16, 16)), 64, 1e-2),
+    ("vcdiff3d_12", lambda: I.vc_diffusion((12, 12, 12), seed=2002), 32, 1e-3),
+    ("convdiff3d_16", lambda: I.convection_diffusion((16, 16, 16), 10.0), 64, 1e-2),
+])
+def test_randomized_matches_oracle(hs, name, mk, leaf, eps):
+    # randomized compression: the sketch G Omega is formed on the device from
+    # the same counter-based Rademacher signs the oracle draws
+    p = mk()
+    fac = _oracle(p, leaf, eps, compress=1)
+    s = hs.Solver.from_problem(p, leaf_size=leaf, symmetric=1 if p.symmetric else 0, compress=1)
+    s.factor(eps, "fp64")
+    assert _ranks_match(s, fac) >= 1
+    b = I.rhs(p.n, 2, seed=1000)
+    ref = H.solve(fac, b.T).T
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out, ref) < 1e-10, _rel(out, ref)
     s.close()
 
 

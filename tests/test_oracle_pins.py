@@ -274,3 +274,37 @@ def test_noise_floor_drops_rounding_level_fill():
     b = I.rhs(p.n, 1, seed=1)[0]
     x = H.solve(_fac(p, 32, 0.0), b)
     np.testing.assert_allclose(p.scipy() @ x, b, atol=1e-11)
+
+
+def test_splitmix64_reference_output():
+    # SplitMix64's published reference stream seeded with 0 starts 0xe220a8397b1dcdaf
+    assert int(H.splitmix64(np.uint64(0))) == 0xE220A8397B1DCDAF
+    Om = H.sketch_matrix(50, 20)
+    np.testing.assert_array_equal(np.abs(Om), 1 / np.sqrt(20))
+    assert abs(Om.mean()) < 0.1 and np.abs(Om.T @ Om - np.eye(20) * 50 / 20).max() < 5
+
+
+@pytest.mark.parametrize("mk,leaf", SMALL)
+def test_randomized_eps0_is_direct(mk, leaf):
+    p = mk()
+    b = I.rhs(p.n, 1, seed=12)[0]
+    x = H.solve(_fac(p, leaf, 0.0, compress=1), b)
+    np.testing.assert_allclose(p.scipy() @ x, b, atol=1e-9 * np.abs(b).max())
+
+
+def test_randomized_ranks_close_and_quality():
+    # the sketch keeps the rank profile close to the exact pivoted QR's and
+    # the preconditioner quality comparable (Sec. 5.3 trend holds too)
+    p = I.poisson((8, 8, 8))
+    A = p.dense()
+    e_ex, e_rd = [], []
+    for eps in [1e-1, 1e-2, 1e-4]:
+        fe = _fac(p, 16, eps, compress=0)
+        fr = _fac(p, 16, eps, compress=1)
+        ke = sum(f.k for f in fe.levels[0].factors.values())
+        kr = sum(f.k for f in fr.levels[0].factors.values())
+        assert abs(ke - kr) <= 0.35 * ke + 4
+        e_ex.append(np.linalg.norm(np.eye(p.n) - H.solve(fe, np.eye(p.n)) @ A, 2))
+        e_rd.append(np.linalg.norm(np.eye(p.n) - H.solve(fr, np.eye(p.n)) @ A, 2))
+    assert e_rd == sorted(e_rd, reverse=True)
+    assert all(r < 30 * e for r, e in zip(e_rd, e_ex))
