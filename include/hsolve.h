@@ -78,6 +78,10 @@ typedef struct {
                              1 = randomized: when the fill block has more than
                              m + 8 columns, pivoted QR of its sketch G Omega
                              (m x (m + 8), Rademacher Omega); default 0 */
+  int32_t cluster_qr;     /* 1 = run the pivoted QR of the fill blocks on
+                             thread-block clusters (distributed shared
+                             memory); 0 = one CTA per cluster; same result
+                             either way; default 1 */
 } hsolve_opts;
 
 typedef struct {

@@ -75,7 +75,8 @@ struct PrepTask {
   int64_t D;        // workspace offset of D = C U^T (k x m, ld m)
   int64_t D2;       // workspace offset of D2 = C^T U^T (general only)
   int l;            // > 0: pivoted QR of the sketch Y (m x l) instead of G
-  int pad;
+  int qr;           // 2: the pivoted QR was done by the cluster kernel (k in
+                    // rank[s], reflectors column-major in W_G); else in-kernel
   int64_t Y;        // workspace offset of the sketch Y (ld m)
 };
 
@@ -145,6 +146,13 @@ struct Launch {
                    real* ws, double* wsd, const int64_t* gptr, const int* gstr,
                    int* rank, double eps, int sym, int max_rank, int maxm,
                    DevError* err, int level, long long* dbg, cudaStream_t st);
+  // thread-block-cluster pivoted QR: cluster size for the largest task (0 =
+  // does not fit), its dynamic shared memory, and the launch
+  static int qr_cluster_size(int maxm, int maxc);
+  static size_t qr_cluster_smem(int maxm, int maxc, int CL);
+  static void qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, int maxc, int CL,
+                         const real* arena, real* ws, double* wsd, const int64_t* gptr,
+                         const int* gstr, int* rank, double eps, int max_rank, cudaStream_t st);
   static void sketch(const SketchTask* tasks_dev, int ntask, int maxm, int maxl,
                      const real* arena, real* ws, const int64_t* gptr, const int* gstr,
                      cudaStream_t st);

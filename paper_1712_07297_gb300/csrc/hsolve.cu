@@ -123,6 +123,12 @@ struct PinnedBuf {
   }
 };
 
+struct ApplyGraph {
+  int nrhs = 0;
+  int nodes = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+
 struct PhaseTimer {
   std::string name;
   double ms = 0;
@@ -178,8 +184,21 @@ struct hsolve_handle {
   int64_t coarse_total = 0;
   // scratch
   DevBuf d_err;
-  DevBuf ws, wsd, blob_dev;
-  PinnedBuf pin;
+  DevBuf ws, wsd, blob_dev, blob2;
+  PinnedBuf pin, pin2;
+  // CUDA graphs of the substitution sweeps, one per nrhs (dropped whenever
+  // the factorization or the level buffers change)
+  bool use_graphs = true;
+  std::vector<ApplyGraph> graphs;
+  cudaStream_t cap_stream = nullptr;
+  void drop_graphs() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
+  ~hsolve_handle() {
+    drop_graphs();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
   DevBuf kry;  // Krylov vectors
   DevBuf dbg;  // per-phase clock stamps of the prep kernel (profiling)
   DevBuf dots;
@@ -449,6 +468,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         sk.push_back(t);
         maxl = std::max(maxl, pt.l);
       }
+      pt.qr = 0;
       pt.wsd = wsd_e;
       wsd_e += 2 * (int64_t)std::max(ncolG, m + kSketchOversample) + 4 * m + 8;
       pt.T = oT[s];
@@ -541,8 +561,42 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     h->wsd.ensure(std::max<int64_t>(wsd_e, 4) * sizeof(double));
     char* d = upload_blob(h, b);
     real* ws = h->ws.as<real>();
+    const PrepTask* d_prep = reinterpret_cast<const PrepTask*>(d + o_prep);
     const int64_t* d_gptr = reinterpret_cast<const int64_t*>(d + o_gptr);
     const int* d_gstr = reinterpret_cast<const int*>(d + o_gstr);
+    // pivoted QR of the fill blocks on thread-block clusters (distributed
+    // shared memory) for every cluster that neither sketches nor has no fill
+    std::vector<PrepTask> qrt;
+    int qm = 0, qc = 0;
+    if (h->opts.cluster_qr) {
+      for (auto& pt : prep)
+        if (pt.l == 0 && pt.ncolG > 0) {
+          qm = std::max(qm, pt.m);
+          qc = std::max(qc, pt.ncolG);
+        }
+    }
+    const int CL = qm > 0 ? Launch<real>::qr_cluster_size(qm, qc) : 0;
+    if (CL > 0)
+      for (auto& pt : prep)
+        if (pt.l == 0 && pt.ncolG > 0) {
+          pt.qr = 2;
+          qrt.push_back(pt);
+        }
+    if (!qrt.empty()) {
+      // the prep tasks changed (qr = 2): upload them again with the QR tasks
+      Blob b2;
+      size_t o2_prep = b2.add(prep), o2_qr = b2.add(qrt);
+      h->blob2.ensure(std::max<size_t>(b2.h.size(), 16));
+      h->pin2.ensure(std::max<size_t>(b2.h.size(), 16));
+      std::memcpy(h->pin2.p, b2.h.data(), b2.h.size());
+      HS_CUDA(cudaMemcpyAsync(h->blob2.p, h->pin2.p, b2.h.size(), cudaMemcpyHostToDevice, h->st));
+      d_prep = reinterpret_cast<const PrepTask*>(h->blob2.as<char>() + o2_prep);
+      timed_lv(h, "qr_cluster", level, 1, [&] {
+        Launch<real>::qr_cluster(reinterpret_cast<const PrepTask*>(h->blob2.as<char>() + o2_qr),
+                                 (int)qrt.size(), qm, qc, CL, arena, ws, h->wsd.as<double>(), d_gptr,
+                                 d_gstr, rank, eps, h->opts.max_rank, h->st);
+      });
+    }
     if (!sk.empty())
       timed_lv(h, "sketch", level, 1, [&] {
         Launch<real>::sketch(reinterpret_cast<const SketchTask*>(d + o_sk), (int)sk.size(), maxm,
@@ -555,7 +609,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       dbg = h->dbg.as<long long>();
     }
     timed_lv(h, "prep", level, 1, [&] {
-      Launch<real>::prep(reinterpret_cast<const PrepTask*>(d + o_prep), nt, arena, fac, ws,
+      Launch<real>::prep(d_prep, nt, arena, fac, ws,
                          h->wsd.as<double>(), d_gptr, d_gstr, rank, eps, sym ? 1 : 0,
                          h->opts.max_rank, maxm, h->d_err.as<DevError>(), level, dbg, h->st);
     });
@@ -834,21 +888,11 @@ void factor_impl(hsolve_handle* h, double eps) {
 // ---------------------------------------------------------------------------
 // Substitution (Alg. 2)
 // ---------------------------------------------------------------------------
+// The level sweeps of Alg. 2 between the level-0 vector and itself: a fixed
+// sequence of launches once the factorization and nrhs are fixed.
 template <typename real>
-void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int64_t ld) {
+void apply_levels(hsolve_handle* h, int nrhs, cudaStream_t st) {
   const int L = (int)h->F.size();
-  for (auto& F : h->F) {
-    if (F->vec_nrhs < nrhs) {
-      const size_t nv = sizeof(real) * (size_t)std::max<int64_t>(F->P.voff[F->P.nclu], 1) * nrhs;
-      F->vec.alloc(nv);
-      F->zvec.alloc(nv);
-      F->part.alloc(sizeof(real) * (size_t)std::max<int64_t>(F->part_elems, 1) * nrhs);
-      F->vec_nrhs = nrhs;
-    }
-  }
-  FLevel& F0 = *h->F[0];
-  const int64_t n0 = F0.P.voff[F0.P.nclu];
-  Launch<real>::perm_in(h->d_perm.as<int64_t>(), h->n, rhs, ld, F0.vec.as<real>(), n0, nrhs, h->st);
   for (int l = 0; l < L; l++) {
     FLevel& F = *h->F[l];
     const int64_t nl = std::max<int64_t>(F.P.voff[F.P.nclu], 1);
@@ -856,12 +900,12 @@ void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int6
       Launch<real>::apply_fwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
                               (int)F.cls[c].size(), F.cls_maxm[c], F.cls_maxnw[c],
                               F.fac.as<real>(), F.vmap.as<int64_t>(), F.vec.as<real>(),
-                              F.zvec.as<real>(), nl, nrhs, h->st);
+                              F.zvec.as<real>(), nl, nrhs, st);
     if (l + 1 < L) {
       FLevel& G = *h->F[l + 1];
       const int64_t ng = std::max<int64_t>(G.P.voff[G.P.nclu], 1);
       Launch<real>::gather_vec(F.next_idx.as<int64_t>(), F.next_n, F.vec.as<real>(), nl,
-                               G.vec.as<real>(), ng, nrhs, h->st);
+                               G.vec.as<real>(), ng, nrhs, st);
     }
   }
   for (int l = L - 1; l >= 0; l--) {
@@ -871,13 +915,62 @@ void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int6
       FLevel& G = *h->F[l + 1];
       const int64_t ng = std::max<int64_t>(G.P.voff[G.P.nclu], 1);
       Launch<real>::scatter_vec(F.next_idx.as<int64_t>(), F.next_n, G.vec.as<real>(), ng,
-                                F.vec.as<real>(), nl, nrhs, h->st);
+                                F.vec.as<real>(), nl, nrhs, st);
     }
     for (int c = (int)F.cls.size() - 1; c >= 0; c--)
       Launch<real>::apply_bwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
                               (int)F.cls[c].size(), F.cls_maxm[c], F.cls_maxnw[c],
                               F.fac.as<real>(), F.vmap.as<int64_t>(), F.vec.as<real>(),
-                              F.zvec.as<real>(), F.part.as<real>(), nl, nrhs, h->st);
+                              F.zvec.as<real>(), F.part.as<real>(), nl, nrhs, st);
+  }
+}
+
+template <typename real>
+void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int64_t ld) {
+  bool realloc = false;
+  for (auto& F : h->F) {
+    if (F->vec_nrhs < nrhs) {
+      const size_t nv = sizeof(real) * (size_t)std::max<int64_t>(F->P.voff[F->P.nclu], 1) * nrhs;
+      F->vec.alloc(nv);
+      F->zvec.alloc(nv);
+      F->part.alloc(sizeof(real) * (size_t)std::max<int64_t>(F->part_elems, 1) * nrhs);
+      F->vec_nrhs = nrhs;
+      realloc = true;
+    }
+  }
+  if (realloc) h->drop_graphs();
+  FLevel& F0 = *h->F[0];
+  const int64_t n0 = F0.P.voff[F0.P.nclu];
+  Launch<real>::perm_in(h->d_perm.as<int64_t>(), h->n, rhs, ld, F0.vec.as<real>(), n0, nrhs, h->st);
+  if (!h->use_graphs) {
+    apply_levels<real>(h, nrhs, h->st);
+  } else {
+    // the sweeps are captured once per nrhs into a CUDA graph (on a private
+    // stream: capture does not execute) and replayed on the caller's stream
+    ApplyGraph* g = nullptr;
+    for (auto& x : h->graphs)
+      if (x.nrhs == nrhs) g = &x;
+    if (!g) {
+      if (!h->cap_stream) HS_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      const int64_t l0 = launches_total();
+      HS_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+      apply_levels<real>(h, nrhs, h->cap_stream);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+      if (e != cudaSuccess) throw Fail(HSOLVE_ERR_CUDA, std::string("apply capture: ") + cudaGetErrorString(e));
+      ApplyGraph ng;
+      ng.nrhs = nrhs;
+      ng.nodes = (int)(launches_total() - l0);
+      e = cudaGraphInstantiate(&ng.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) throw Fail(HSOLVE_ERR_CUDA, std::string("apply graph: ") + cudaGetErrorString(e));
+      // capture counted the launches once; replays add them below
+      count_launch(-ng.nodes);
+      h->graphs.push_back(ng);
+      g = &h->graphs.back();
+    }
+    HS_CUDA(cudaGraphLaunch(g->exec, h->st));
+    count_launch(g->nodes);
   }
   Launch<real>::perm_out(h->d_perm.as<int64_t>(), h->n, F0.vec.as<real>(), n0, out, ld, nrhs, h->st);
 }
@@ -1254,6 +1347,7 @@ void hsolve_default_opts(hsolve_opts* o) {
   o->max_rank = 0;
   o->gmres_restart = 50;
   o->compress = 0;
+  o->cluster_qr = 1;
 }
 
 hsolve_status hsolve_analyze(const hsolve_csr* A, const double* coords, int dim,
@@ -1375,6 +1469,7 @@ hsolve_status hsolve_factor(hsolve_handle* h, double eps, hsolve_precision prec)
   if (!(eps >= 0.0) || prec < HSOLVE_FP64 || prec > HSOLVE_MIXED_BF16)
     return set_err(h, HSOLVE_ERR_ARG, "bad eps or precision");
   h->factored = false;
+  h->drop_graphs();
   h->F.clear();
   try {
     h->prec = prec;

@@ -579,9 +579,11 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
 
   mark(1);
   const bool sketched = tk.l > 0;
+  const bool qr_done = tk.qr == 2;  // done by the thread-block-cluster kernel
   // ---- gather the nonzero fill columns into G (Eq. lra input), row-major
-  // (not needed when the pivoted QR runs on the sketch Y = G Omega)
-  if (!sketched) {
+  // (not needed when the pivoted QR runs on the sketch Y = G Omega or was
+  // done by the cluster kernel)
+  if (!sketched && !qr_done) {
     const int nc = tk.ncolG;
     // flag nonzero columns: one thread per column, batched independent loads
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
@@ -642,7 +644,9 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
   int k = 0;
   int kmax = m;
   if (max_rank > 0) kmax = min(kmax, max_rank);
-  if (sketched) {
+  if (qr_done) {
+    k = rank[tk.s];
+  } else if (sketched) {
     // pivoted QR of the sketch (column-major m x l), in the shared memory of
     // the not yet used A_ss^{-1} and [U V] buffers when it fits; the kept
     // reflectors then move to W_G (column-major, ld m) for U
@@ -656,6 +660,7 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
     k = cta_householder_qr<real, true>(m, ncol, W_G, ncol, nrm2, orig, tau, true, eps, kmax,
                                        noise_rtol * s_amax, red_d, red_i, vsh, rsign);
   }
+  __syncthreads();
   if (threadIdx.x == 0) rank[tk.s] = k;
   mark(3);
   if (k == m) return;  // untouched: all unknowns coarse, E_s = I
@@ -697,7 +702,7 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
 
   mark(4);
   // ---- U = first k columns of Q of the pivoted QR
-  if (sketched)
+  if (sketched || qr_done)
     cta_form_q<real, false>(m, k, W_G, m, tau, 0, k, W_U, m, vsh);
   else
     cta_form_q<real, true>(m, k, W_G, ncol, tau, 0, k, W_U, m, vsh);

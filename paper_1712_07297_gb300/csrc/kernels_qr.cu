@@ -1,0 +1,296 @@
+// Truncated column-pivoted Householder QR of a cluster's fill block (Eq. lra)
+// spread over a thread-block cluster.
+//
+// The fill block G (m x c, c often in the thousands) is split by columns over
+// the CL CTAs of a cluster; each CTA keeps its nonzero columns in its own
+// shared memory for the whole factorization, so every step streams shared
+// memory instead of L2.  Per step the CTAs agree on the pivot through
+// distributed shared memory: the largest remaining column norm over the
+// cluster, then the lowest original column index among the columns within
+// 1e-10 of it (the tie rule of the single-CTA path); the owner CTA forms the
+// reflector, every CTA reads it from the owner's shared memory and updates
+// its columns.  Three cluster barriers per step; every CTA takes the same
+// branches (its decisions use the same exchanged values), so the barriers
+// always match.
+//
+// Outputs, in the layout the per-cluster kernel expects: the rank k in
+// rank[s], the reflectors v_j as column j of W_G (column-major, ld m, rows
+// j..m), tau_j and the sign of R's diagonal in the per-cluster double
+// workspace.
+#include <climits>
+#include <cooperative_groups.h>
+
+#include "common.h"
+
+namespace cg = cooperative_groups;
+
+namespace hs {
+
+namespace {
+
+constexpr double kTieRtol = 1e-10;
+
+// Dynamic shared memory of one CTA: every array starts on a 16-byte boundary
+// (the same computation sizes the launch and carves the buffer).
+struct QrSmem {
+  size_t G, nrm, oidx, tpos, vbuf, vloc, total;
+  __host__ __device__ static size_t al(size_t b) { return (b + 15) / 16 * 16; }
+  __host__ __device__ QrSmem(int ldsm, int cc, int sz) {
+    G = 0;
+    nrm = G + al((size_t)ldsm * cc * sz);
+    oidx = nrm + al((size_t)cc * sizeof(double));
+    tpos = oidx + al((size_t)cc * sizeof(int));
+    vbuf = tpos + al((size_t)cc * sizeof(int));
+    vloc = vbuf + al((size_t)ldsm * sz);
+    total = vloc + al((size_t)ldsm * sz);
+  }
+};
+
+struct Exchange {
+  double val;      // largest local squared norm
+  double candnrm;  // squared norm of the local candidate
+  double tau;      // owner: 2 / v^T v of the step's reflector
+  int cand;        // lowest original index among the local candidates
+  int loc;         // local column of the candidate
+};
+
+__device__ double block_max(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ int block_min(int v, int* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = min(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  int r = red[0];
+  __syncthreads();
+  return r;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256)
+qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ arena,
+                  real* __restrict__ ws_all, double* __restrict__ wsd_all,
+                  const int64_t* __restrict__ gptr, const int* __restrict__ gstr, int* rank,
+                  double eps, double noise_rtol, int max_rank, int ldsm, int ccmax) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks();
+  const int cr = (int)cl.block_rank();
+  const PrepTask tk = tasks[blockIdx.x / CL];
+  const int m = tk.m, c = tk.ncolG;
+  __shared__ double red_d[256];
+  __shared__ int red_i[256];
+  __shared__ Exchange xch;
+  __shared__ int s_nloc, s_loc;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const QrSmem lay(ldsm, ccmax, (int)sizeof(real));
+  real* Gs = reinterpret_cast<real*>(dsm + lay.G);  // ldsm x ccmax, column-major
+  double* nrm = reinterpret_cast<double*>(dsm + lay.nrm);
+  int* oidx = reinterpret_cast<int*>(dsm + lay.oidx);
+  int* tpos = reinterpret_cast<int*>(dsm + lay.tpos);
+  real* vbuf = reinterpret_cast<real*>(dsm + lay.vbuf);  // the owner's reflector
+  real* vloc = reinterpret_cast<real*>(dsm + lay.vloc);  // this CTA's copy
+
+  // per-cluster outputs (same layout as the per-cluster kernel)
+  double* nrm2_g = wsd_all + tk.wsd;
+  real* tau_g = reinterpret_cast<real*>(nrm2_g + 2 * (int64_t)tk.ncolG);
+  real* rsign_g = tau_g + 2 * m;
+  real* W_G = ws_all + tk.ws + 10 * (int64_t)m * m;
+
+  // scale of the rounding-noise floor: max |A_ss|
+  double amx = 0;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x)
+    amx = fmax(amx, fabs((double)arena[tk.a_ss + idx % m + (int64_t)(idx / m) * tk.ld]));
+  const double floor = noise_rtol * block_max(amx, red_d);
+
+  // this CTA's share of the gathered columns; keep the nonzero ones
+  const int cc = (c + CL - 1) / CL;
+  const int q0 = min(c, cr * cc), q1 = min(c, q0 + cc);
+  const int nq = q1 - q0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int t = warp; t < nq; t += nwarp) {
+    const int64_t p = gptr[tk.gcol + q0 + t];
+    const int st = gstr[tk.gcol + q0 + t];
+    bool nz = false;
+    for (int i = lane; i < m; i += 32) nz |= (arena[p + (int64_t)i * st] != real(0));
+    nz = __any_sync(0xffffffffu, nz);
+    if (lane == 0) tpos[t] = nz ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int t = 0; t < nq; t++) tpos[t] = tpos[t] ? n++ : -1;
+    s_nloc = n;
+  }
+  __syncthreads();
+  const int nloc = s_nloc;
+  for (int t = warp; t < nq; t += nwarp) {
+    const int d = tpos[t];
+    if (d < 0) continue;
+    const int64_t p = gptr[tk.gcol + q0 + t];
+    const int st = gstr[tk.gcol + q0 + t];
+    for (int i = lane; i < m; i += 32) Gs[i + (int64_t)d * ldsm] = arena[p + (int64_t)i * st];
+    if (lane == 0) oidx[d] = q0 + t;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
+    double s = 0;
+    for (int i = 0; i < m; i++) {
+      double x = Gs[i + (int64_t)t * ldsm];
+      s += x * x;
+    }
+    nrm[t] = s;
+  }
+  __syncthreads();
+
+  const int kmax = max_rank > 0 ? min(m, max_rank) : m;
+  const int steps = min(m, c);
+  double r11 = 0;
+  int k = 0;
+  for (int j = 0; j < steps; j++) {
+    // 1. largest remaining norm over the cluster
+    double lmx = 0;
+    for (int t = threadIdx.x; t < nloc; t += blockDim.x) lmx = fmax(lmx, nrm[t]);
+    lmx = block_max(lmx, red_d);
+    if (threadIdx.x == 0) xch.val = lmx;
+    cl.sync();
+    double M = 0;
+    for (int rr = 0; rr < CL; rr++) M = fmax(M, cl.map_shared_rank(&xch, rr)->val);
+    if (M <= 0.0) break;
+    // 2. lowest original index among the near-maximal columns
+    int lc = INT_MAX;
+    for (int t = threadIdx.x; t < nloc; t += blockDim.x)
+      if (nrm[t] >= (1.0 - kTieRtol) * M && oidx[t] < lc) lc = oidx[t];
+    lc = block_min(lc, red_i);
+    if (lc != INT_MAX)
+      for (int t = threadIdx.x; t < nloc; t += blockDim.x)
+        if (oidx[t] == lc) s_loc = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      xch.cand = lc;
+      xch.loc = (lc != INT_MAX) ? s_loc : -1;
+      xch.candnrm = (lc != INT_MAX) ? nrm[s_loc] : -1.0;
+    }
+    cl.sync();
+    int best = INT_MAX, owner = 0;
+    for (int rr = 0; rr < CL; rr++) {
+      const int x = cl.map_shared_rank(&xch, rr)->cand;
+      if (x < best) {
+        best = x;
+        owner = rr;
+      }
+    }
+    const double r = sqrt(cl.map_shared_rank(&xch, owner)->candnrm);
+    if (j == 0) r11 = r;
+    if (r <= floor || (eps > 0.0 && r <= eps * r11) || j >= kmax) break;
+    // 3. the owner forms the reflector v = x - beta e1, beta = -sign(x0) ||x||
+    if (cr == owner) {
+      const int loc = xch.loc;
+      const double x0 = (double)Gs[j + (int64_t)loc * ldsm];
+      const double beta = (x0 >= 0.0) ? -r : r;
+      const double tj = (r > 0.0) ? 1.0 / (r * (r + fabs(x0))) : 0.0;
+      for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+        const real v = (i == j) ? (real)(x0 - beta) : Gs[i + (int64_t)loc * ldsm];
+        vbuf[i] = v;
+        W_G[i + (int64_t)j * m] = v;
+      }
+      if (threadIdx.x == 0) {
+        xch.tau = tj;
+        tau_g[j] = (real)tj;
+        rsign_g[j] = beta < 0.0 ? real(-1) : real(1);
+        nrm[loc] = -1.0;  // used: out of every later step
+      }
+    }
+    cl.sync();
+    // 4. every CTA applies the reflector to its remaining columns and
+    //    recomputes their squared norms over rows j+1..m
+    const real* ov = cl.map_shared_rank(vbuf, owner);
+    const real tj = (real)cl.map_shared_rank(&xch, owner)->tau;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) vloc[i] = ov[i];
+    __syncthreads();
+    for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
+      if (nrm[t] < 0.0) continue;
+      real* col = Gs + (int64_t)t * ldsm;
+      real w = 0;
+      for (int i = j; i < m; i++) w += vloc[i] * col[i];
+      w *= tj;
+      double s = 0;
+      for (int i = j; i < m; i++) {
+        const real v = col[i] - w * vloc[i];
+        col[i] = v;
+        if (i > j) s += (double)v * (double)v;
+      }
+      nrm[t] = s;
+    }
+    __syncthreads();
+    k = j + 1;
+  }
+  if (cr == 0 && threadIdx.x == 0) rank[tk.s] = k;
+  // no CTA leaves while another may still read its shared memory
+  cl.sync();
+}
+
+}  // namespace
+
+template <typename real>
+int Launch<real>::qr_cluster_size(int maxm, int maxc) {
+  for (int CL = 1; CL <= 16; CL *= 2) {
+    if (qr_cluster_smem(maxm, maxc, CL) <= 200 * 1024) return CL;
+  }
+  return 0;
+}
+
+template <typename real>
+size_t Launch<real>::qr_cluster_smem(int maxm, int maxc, int CL) {
+  const int cc = (maxc + CL - 1) / CL;
+  return QrSmem(maxm + 1, cc, (int)sizeof(real)).total;
+}
+
+template <typename real>
+void Launch<real>::qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, int maxc, int CL,
+                              const real* arena, real* ws, double* wsd, const int64_t* gptr,
+                              const int* gstr, int* rank, double eps, int max_rank,
+                              cudaStream_t st) {
+  if (ntask <= 0) return;
+  const double noise_rtol = sizeof(real) == 8 ? 1e-14 : 1e-6;
+  const size_t smem = qr_cluster_smem(maxm, maxc, CL);
+  const int cc = (maxc + CL - 1) / CL;
+  cudaFuncSetAttribute(qr_cluster_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)std::max<size_t>(smem, 48 * 1024));
+  if (CL > 8)
+    cudaFuncSetAttribute(qr_cluster_kernel<real>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int t0 = 0; t0 < ntask; t0 += 4096) {
+    const int nt = std::min(4096, ntask - t0);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nt * CL);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launch();
+    cudaLaunchKernelEx(&cfg, qr_cluster_kernel<real>, tasks_dev + t0, arena, ws, wsd, gptr, gstr,
+                       rank, eps, noise_rtol, max_rank, maxm + 1, cc);
+  }
+}
+
+template struct Launch<double>;
+template struct Launch<float>;
+
+}  // namespace hs

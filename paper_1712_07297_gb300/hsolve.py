@@ -37,7 +37,8 @@ class Csr(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("symmetric", C.c_int32), ("top_size", C.c_int64),
-                ("max_rank", C.c_int32), ("gmres_restart", C.c_int32), ("compress", C.c_int32)]
+                ("max_rank", C.c_int32), ("gmres_restart", C.c_int32), ("compress", C.c_int32),
+                ("cluster_qr", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -133,7 +134,7 @@ class Solver:
     """One analysed matrix: analyze -> factor -> apply / solve."""
 
     def __init__(self, rowptr, col, val, coords=None, *, leaf_size=128, symmetric=-1, top_size=0,
-                 max_rank=0, gmres_restart=50, compress=0, stream=None):
+                 max_rank=0, gmres_restart=50, compress=0, cluster_qr=1, stream=None):
         lib = load()
         self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         self.col = np.ascontiguousarray(col, dtype=np.int32)
@@ -144,6 +145,7 @@ class Solver:
         o = default_opts()
         o.leaf_size, o.symmetric, o.top_size = leaf_size, symmetric, top_size
         o.max_rank, o.gmres_restart, o.compress = max_rank, gmres_restart, compress
+        o.cluster_qr = cluster_qr
         h = C.c_void_p()
         cptr, dim = None, 0
         if coords is not None:

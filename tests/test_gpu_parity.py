@@ -248,3 +248,22 @@ def test_host_solve_api(hs):
     x, info = s.solve_host(b, krylov="pcg", tol=1e-10)
     assert np.linalg.norm(b - p.scipy() @ x) <= 1.0001e-10 * np.linalg.norm(b)
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_fp32"])
+def test_cluster_qr_equals_single_cta(hs, precision):
+    # the pivoted QR on thread-block clusters (distributed shared memory) and
+    # the one-CTA-per-cluster path take the same decisions and produce the
+    # same factorization
+    p = I.poisson((20, 20, 20))
+    b = torch.from_numpy(I.rhs(p.n, 1, seed=31)).cuda()
+    outs, ranks = [], []
+    for cq in (0, 1):
+        s = hs.Solver.from_problem(p, leaf_size=64, symmetric=1, cluster_qr=cq)
+        s.factor(1e-2, precision)
+        ranks.append([list(s.level(l)[1]) for l in range(s.stats()["levels"])])
+        outs.append(s.apply(b).cpu().numpy())
+        s.close()
+    assert ranks[0] == ranks[1]
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert _rel(outs[1], outs[0]) < tol
