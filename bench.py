@@ -130,7 +130,7 @@ def run_gpu(args, rank, world):
     nrhs = args.nrhs or st["nrhs"]
     stream = torch.cuda.current_stream()
     s = hsolve.Solver.from_problem(prob, leaf_size=leaf, symmetric=1 if prob.spd else 0,
-                                   stream=stream)
+                                   top_size=args.top_size, stream=stream)
     krylov = "pcg" if prob.spd else "gmres"
     b_host = I.rhs(prob.n, nrhs, seed=st["rhs_seed"])
     b = torch.from_numpy(b_host).cuda()
@@ -200,6 +200,10 @@ def run_gpu(args, rank, world):
     dom = max((k for k in ph64 if k not in ("upload", "assemble")), key=lambda k: ph64[k][0])
     work = {"schur": st64["schur_flops"], "prep": st64["prep_flops"],
             "gemm_coarse": st64["gemm_flops"], "gemm_fill": st64["gemm_flops"]}
+    if "dense_top" in ph64:
+        n_top = st64["top_size"]
+        work["dense_top"] = 2.0 / 3.0 * n_top ** 3
+        work["prep"] = st64["prep_flops"] - work["dense_top"]
     ms_dom, nl_dom = ph64[dom]
     fl = work.get(dom, st64["factor_flops"])
     ach = fl / (ms_dom * 1e-3) / 1e12
@@ -226,7 +230,8 @@ def run_gpu(args, rank, world):
         "config": {"workload": "3D 7-point Poisson 64^3 (N=262144), clusters of 128, eps=1e-2, "
                                "1 RHS U[-1,1], PCG to 1e-10",
                    "n": prob.n, "nnz": prob.nnz, "leaf": leaf, "eps": eps, "nrhs": nrhs,
-                   "krylov": krylov, "l2": "flushed between timed steps (256 MB write)",
+                   "krylov": krylov, "top_size": args.top_size,
+                   "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iterations": i64[-1].iterations,
         "rel_residual": max(i.rel_residual for i in i64),
@@ -271,11 +276,11 @@ A = p.scipy()
 ts = []
 for _ in range(%d):
     t0 = time.perf_counter()
-    fac = H.factor(p.rowptr, p.col, p.val, p.coords, 128, %r, symmetric=True)
+    fac = H.factor(p.rowptr, p.col, p.val, p.coords, 128, %r, symmetric=True, top_size=%d)
     x, it, res = K.pcg(A, b, lambda r: H.solve(fac, r), tol=1e-10, maxit=500)
     ts.append(time.perf_counter() - t0)
 print(json.dumps({"s": ts, "it": it, "res": res}))
-""" % (ROOT, steps, args.eps if args.eps is not None else 1e-2)
+""" % (ROOT, steps, args.eps if args.eps is not None else 1e-2, args.top_size)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         return None, r.stderr[-400:]
@@ -294,6 +299,8 @@ def main():
     ap.add_argument("--nrhs", type=int, default=0)
     ap.add_argument("--mixed", default="mixed_fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--top-size", dest="top_size", type=int, default=8192,
+                    help="factor a level densely once it holds at most this many unknowns")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

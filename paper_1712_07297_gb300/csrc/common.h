@@ -60,6 +60,37 @@ int round_up(int x, int a);
 // Kernel launch wrappers (kernels.cu).  `real` is float or double.
 // ---------------------------------------------------------------------------
 
+// A run of gathered columns taken from one block of the level arena.  The
+// gathered matrices of a cluster (its fill columns G, its neighbour columns
+// A_sN, and their transposed counterparts in the general case) are lists of
+// such runs; kernels resolve a gathered column index to (offset, stride).
+struct Seg {
+  int64_t off;    // arena offset of the block
+  int colstart;   // first gathered column index of the run
+  int ld;         // leading dimension of the block
+  int trans;      // 0: gathered column = block column, rows contiguous;
+                  // 1: gathered column = block row (stride ld)
+  int pad;
+};
+
+__host__ __device__ inline void seg_col(const Seg* sg, int nseg, int j, int64_t* p, int* st) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sg[mid].colstart <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  const Seg& g = sg[lo];
+  const int q = j - g.colstart;
+  if (g.trans) {
+    *p = g.off + q;
+    *st = g.ld;
+  } else {
+    *p = g.off + (int64_t)q * g.ld;
+    *st = 1;
+  }
+}
+
 // Per-cluster task of the dense "prep" phase.
 struct PrepTask {
   int s;            // level-local cluster id
@@ -67,7 +98,7 @@ struct PrepTask {
   int ld;           // ld of cluster s's block rows
   int ncolG;        // fill columns gathered into G
   int64_t a_ss;     // offset of block (s,s) in the arena
-  int64_t gcol;     // offset into the column-descriptor arrays
+  int64_t gcol;     // offset of the fill-column runs (Seg list)
   int64_t ws;       // workspace offset (elements of real)
   int64_t wsd;      // workspace offset (doubles) for norms
   int64_t T;        // factor offset of T' (m x m, ld m)
@@ -78,26 +109,29 @@ struct PrepTask {
   int qr;           // 2: the pivoted QR was done by the cluster kernel (k in
                     // rank[s], reflectors column-major in W_G); else in-kernel
   int64_t Y;        // workspace offset of the sketch Y (ld m)
+  int ngcol;        // number of fill-column runs
+  int pad2;
 };
 
 // Sketch task: Y (m x l, ld m) = G Omega for the gathered fill columns of
 // one cluster, Omega[q, j] = +-1/sqrt(l) (splitmix64 sign of (q << 32) | j).
 struct SketchTask {
-  int m, l, ncol, pad;
-  int64_t gcol;     // offset into the column-descriptor arrays
+  int m, l, ncol, nseg;
+  int64_t gcol;     // offset of the fill-column runs (Seg list)
   int64_t Y;        // workspace offset of Y
 };
 
-// Grouped GEMM task: C (M x N, ldc) = A (M x K, lda) * Bg, where column j of
-// Bg starts at bptr[j] with element stride bstr[j].  M, N, K may be bounded
-// by the device rank array: see kernels.cu.
+// Grouped GEMM task: C (M x N, ldc) = A (M x K, lda) * Bg, where the columns
+// of Bg are the gathered columns of a Seg list.  M, N, K may be bounded by
+// the device rank array: see kernels_misc.cu.
 struct GemmTask {
   int s;
   int M, N, K;         // upper bounds (rows of A, columns of Bg, inner)
-  int mode;            // how M/K derive from the rank k = rank[s] (see kernels.cu)
+  int mode;            // how M/K derive from the rank k = rank[s] (see kernels_misc.cu)
   int lda, ldc;
+  int nseg;            // runs of Bg
   int64_t A, C;        // offsets (A in factor or workspace arena, C in ws/factor)
-  int64_t bcol;        // offset into column descriptor arrays
+  int64_t bcol;        // offset of Bg's runs (Seg list)
 };
 
 // Schur update task: C_mapped -= P^T Q with P, Q (f x nw, ld ldy) taken
@@ -108,7 +142,7 @@ struct SchurTask {
   int nw;           // sum of neighbour widths
   int nb;           // neighbours
   int64_t P, Q;     // factor offsets of the P/Q storages
-  int64_t map;      // offset into the packed row/col map array (nw entries)
+  int64_t map;      // offset of the neighbour runs (Seg list, nb entries)
   int64_t base;     // offset into the block-base table (nb*nb entries)
   int64_t ldn;      // offset into the neighbour-ld array (nb entries)
 };
@@ -143,7 +177,7 @@ struct ApplyRec {   // one cluster's factor, as the substitution sweeps use it
 template <typename real>
 struct Launch {
   static void prep(const PrepTask* tasks_dev, int ntask, real* arena, real* fac,
-                   real* ws, double* wsd, const int64_t* gptr, const int* gstr,
+                   real* ws, double* wsd, const Seg* segs,
                    int* rank, double eps, int sym, int max_rank, int maxm,
                    DevError* err, int level, long long* dbg, cudaStream_t st);
   // thread-block-cluster pivoted QR: cluster size for the largest task (0 =
@@ -151,17 +185,16 @@ struct Launch {
   static int qr_cluster_size(int maxm, int maxc);
   static size_t qr_cluster_smem(int maxm, int maxc, int CL);
   static void qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, int maxc, int CL,
-                         const real* arena, real* ws, double* wsd, const int64_t* gptr,
-                         const int* gstr, int* rank, double eps, int max_rank, cudaStream_t st);
+                         const real* arena, real* ws, double* wsd, const Seg* segs, int* rank, double eps, int max_rank, cudaStream_t st);
   static void sketch(const SketchTask* tasks_dev, int ntask, int maxm, int maxl,
-                     const real* arena, real* ws, const int64_t* gptr, const int* gstr,
+                     const real* arena, real* ws, const Seg* segs,
                      cudaStream_t st);
   static void gemm_gather(const GemmTask* tasks_dev, int ntask, int maxM, int maxN,
                           const real* Abase, real* Cbase, const real* Bbase,
-                          const int64_t* bptr, const int* bstr, const int* rank,
+                          const Seg* segs, const int* rank,
                           cudaStream_t st);
   static void schur(const SchurTask* tasks_dev, int ntask, int maxnw, const real* fac,
-                    real* arena, const int* map, const int64_t* base, const int* ldn,
+                    real* arena, const Seg* segs, const int64_t* base, const int* ldn,
                     const int* rank, cudaStream_t st);
   static void scatter(const ScatterSeg* segs_dev, int nseg, int maxw, const real* src,
                       real* arena, const int* rank, cudaStream_t st);
@@ -183,10 +216,10 @@ struct Launch {
                       real* dst, int64_t ldd, int nrhs, cudaStream_t st);
   static void perm_out(const int64_t* perm, int64_t n, const real* src, int64_t lds,
                        double* dst, int64_t ldd, int nrhs, cudaStream_t st);
-  static void dense_top_factor(real* a, int n, int sym, int* piv, DevError* err,
-                               cudaStream_t st);
-  static void dense_top_solve(const real* a, int n, int sym, const int* piv, real* y,
-                              int64_t ldy, int nrhs, cudaStream_t st);
+  // Dense top of an SPD factorization: A (n x n, ld lda) is overwritten by
+  // its Cholesky factor L; X (n x n, ld n) receives L^{-1}.
+  static void dense_top(real* A, int64_t lda, int n, real* X, DevError* err, int level,
+                        cudaStream_t st);
 };
 
 // float64 Krylov helpers (kernels.cu)

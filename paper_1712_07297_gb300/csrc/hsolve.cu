@@ -25,6 +25,7 @@ using namespace hs;
 namespace {
 
 constexpr int kSketchOversample = 8;  // sketch width m + 8 (randomized Eq. lra)
+constexpr int kTopOneCta = 256;       // larger single SPD clusters: blocked dense top
 
 // ---------------------------------------------------------------------------
 // Small helpers
@@ -362,7 +363,28 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   std::vector<int64_t> vmap;
   std::vector<int> fillcols(nc, 0), fillw(nc, 0);
   FL.cls.clear();
-  for (size_t c = 0; c < P.classes.size(); c++) {
+  // a single large SPD cluster (the dense top of Alg. 1) goes to the blocked
+  // multi-CTA Cholesky and inverse factor: E_s = I, k = 0, no neighbours
+  const bool dense_top = (nc == 1 && sym && cur[0] > kTopOneCta);
+  if (dense_top) {
+    const int n = cur[0];
+    timed_lv(h, "dense_top", level, 0, [&] {
+      Launch<real>::dense_top(arena + P.off[P.find(0, 0)], P.ld[0], n, fac + oT[0],
+                              h->d_err.as<DevError>(), level, h->st);
+    });
+    check_dev_error(h);
+    FL.cls.push_back({0});
+    FL.k[0] = 0;
+    cur[0] = 0;
+    ApplyRec& r = recs[0];
+    r.m = n; r.k = 0; r.nw = 0; r.sym = 1; r.voff = 0;
+    r.T = oT[0]; r.TR = oT[0]; r.Y = oY[0]; r.XT = oY[0]; r.map = 0;
+    const double nf = n;
+    h->prep_flops += 2.0 / 3.0 * nf * nf * nf;
+    h->factor_flops += 2.0 / 3.0 * nf * nf * nf;
+    h->apply_bytes += (int64_t)sizeof(real) * 2 * ((int64_t)n * n + 2 * (int64_t)n);
+  }
+  for (size_t c = 0; c < P.classes.size() && !dense_top; c++) {
     std::vector<int> S;
     for (int s : P.classes[c])
       if (cur[s] > 0) S.push_back(s);
@@ -375,9 +397,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     std::vector<GemmTask> gY, gXT, gE, gE2;
     std::vector<SchurTask> sch;
     std::vector<ScatterSeg> segN, segW;
-    std::vector<int64_t> gptr;
-    std::vector<int> gstr;
-    std::vector<int> smap;
+    std::vector<Seg> segs;  // runs of gathered columns, task by task
     std::vector<int64_t> sbase;
     std::vector<int> sld;
     int64_t ws_e = 0, wsd_e = 0;
@@ -403,34 +423,32 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       fillcols[s] = sym ? nwf : 2 * nwf;
       maxnw = std::max(maxnw, nw);
       maxnwf = std::max(maxnwf, nwf);
-      // G column descriptors: columns of A_sw, then (general) rows of A_ws
-      const int64_t gcol = (int64_t)gptr.size();
-      for (auto& e : W)
-        for (int q = 0; q < e.w; q++) {
-          gptr.push_back(e.p_sj + (int64_t)q * P.ld[s]);
-          gstr.push_back(1);
+      // gathered-column runs, one per block: G = [A_sw columns, (general)
+      // rows of A_ws]; its first nfs runs alone are A_sW (for C U^T A_sW);
+      // A_ws^T alone (for the general far-to-coarse product); A_sN columns;
+      // (general) rows of A_Ns
+      auto add_runs = [&](const std::vector<Nb>& L, bool trans, int c0) {
+        for (auto& e : L) {
+          Seg g{};
+          g.off = trans ? e.p_js : e.p_sj;
+          g.colstart = c0;
+          g.ld = trans ? P.ld[e.j] : P.ld[s];
+          g.trans = trans ? 1 : 0;
+          segs.push_back(g);
+          c0 += e.w;
         }
-      if (!sym)
-        for (auto& e : W)
-          for (int q = 0; q < e.w; q++) {
-            gptr.push_back(e.p_js + q);
-            gstr.push_back(P.ld[e.j]);
-          }
+      };
+      const int64_t gcol = (int64_t)segs.size();
+      add_runs(W, false, 0);
+      if (!sym) add_runs(W, true, nwf);
+      const int ngcol = (int)(segs.size() - gcol);
+      const int64_t gcolT = (int64_t)segs.size();
+      if (!sym) add_runs(W, true, 0);
       const int ncolG = sym ? nwf : 2 * nwf;
-      // neighbour column descriptors (A_sN columns, then rows of A_Ns)
-      const int64_t ncol0 = (int64_t)gptr.size();
-      for (auto& e : N)
-        for (int q = 0; q < e.w; q++) {
-          gptr.push_back(e.p_sj + (int64_t)q * P.ld[s]);
-          gstr.push_back(1);
-        }
-      const int64_t ncol1 = (int64_t)gptr.size();
-      if (!sym)
-        for (auto& e : N)
-          for (int q = 0; q < e.w; q++) {
-            gptr.push_back(e.p_js + q);
-            gstr.push_back(P.ld[e.j]);
-          }
+      const int64_t ncol0 = (int64_t)segs.size();
+      add_runs(N, false, 0);
+      const int64_t ncol1 = (int64_t)segs.size();
+      if (!sym) add_runs(N, true, 0);
       // workspace
       const int64_t mm = (int64_t)m * m;
       PrepTask& pt = prep[t];
@@ -440,6 +458,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       pt.ncolG = ncolG;
       pt.a_ss = P.off[P.find(s, s)];
       pt.gcol = gcol;
+      pt.ngcol = ngcol;
       pt.ws = ws_e;
       ws_e += 11 * mm + (int64_t)m * ncolG;
       pt.D = ws_e;
@@ -464,6 +483,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         t.l = pt.l;
         t.ncol = ncolG;
         t.gcol = gcol;
+        t.nseg = ngcol;
         t.Y = pt.Y;
         sk.push_back(t);
         maxl = std::max(maxl, pt.l);
@@ -477,7 +497,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       if (nw > 0) {
         GemmTask g{};
         g.s = s; g.M = m; g.N = nw; g.K = m; g.mode = 0; g.lda = m; g.ldc = m;
-        g.A = oT[s]; g.C = oY[s]; g.bcol = ncol0;
+        g.A = oT[s]; g.C = oY[s]; g.bcol = ncol0; g.nseg = (int)N.size();
         gY.push_back(g);
         if (!sym) {
           g.A = oTR[s]; g.C = oXT[s]; g.bcol = ncol1;
@@ -488,10 +508,10 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       if (nwf > 0) {
         GemmTask g{};
         g.s = s; g.M = m; g.N = nwf; g.K = m; g.mode = 1; g.lda = m; g.ldc = m;
-        g.A = pt.D; g.C = Eoff; g.bcol = gcol;
+        g.A = pt.D; g.C = Eoff; g.bcol = gcol; g.nseg = (int)W.size();
         gE.push_back(g);
         if (!sym) {
-          g.A = pt.D2; g.C = E2off; g.bcol = gcol + nwf;
+          g.A = pt.D2; g.C = E2off; g.bcol = gcolT;
           gE2.push_back(g);
         }
       }
@@ -526,9 +546,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         sc.s = s; sc.m = m; sc.nw = nw; sc.nb = (int)N.size();
         sc.P = sym ? oY[s] : oXT[s];
         sc.Q = oY[s];
-        sc.map = (int64_t)smap.size();
-        for (int a = 0; a < (int)N.size(); a++)
-          for (int q = 0; q < N[a].w; q++) smap.push_back((a << 20) | q);
+        sc.map = ncol0;  // the A_sN runs: one per neighbour, colstart = its offset
         sc.base = (int64_t)sbase.size();
         for (int a = 0; a < (int)N.size(); a++)
           for (int b = 0; b < (int)N.size(); b++) {
@@ -555,15 +573,13 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     size_t o_sk = b.add(sk);
     size_t o_prep = b.add(prep), o_gY = b.add(gY), o_gXT = b.add(gXT), o_gE = b.add(gE),
            o_gE2 = b.add(gE2), o_sch = b.add(sch), o_segN = b.add(segN), o_segW = b.add(segW),
-           o_gptr = b.add(gptr), o_gstr = b.add(gstr), o_smap = b.add(smap),
-           o_sbase = b.add(sbase), o_sld = b.add(sld);
+           o_segs = b.add(segs), o_sbase = b.add(sbase), o_sld = b.add(sld);
     h->ws.ensure(std::max<int64_t>(ws_e, 4) * sizeof(real));
     h->wsd.ensure(std::max<int64_t>(wsd_e, 4) * sizeof(double));
     char* d = upload_blob(h, b);
     real* ws = h->ws.as<real>();
     const PrepTask* d_prep = reinterpret_cast<const PrepTask*>(d + o_prep);
-    const int64_t* d_gptr = reinterpret_cast<const int64_t*>(d + o_gptr);
-    const int* d_gstr = reinterpret_cast<const int*>(d + o_gstr);
+    const Seg* d_segs = reinterpret_cast<const Seg*>(d + o_segs);
     // pivoted QR of the fill blocks on thread-block clusters (distributed
     // shared memory) for every cluster that neither sketches nor has no fill
     std::vector<PrepTask> qrt;
@@ -593,14 +609,14 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       d_prep = reinterpret_cast<const PrepTask*>(h->blob2.as<char>() + o2_prep);
       timed_lv(h, "qr_cluster", level, 1, [&] {
         Launch<real>::qr_cluster(reinterpret_cast<const PrepTask*>(h->blob2.as<char>() + o2_qr),
-                                 (int)qrt.size(), qm, qc, CL, arena, ws, h->wsd.as<double>(), d_gptr,
-                                 d_gstr, rank, eps, h->opts.max_rank, h->st);
+                                 (int)qrt.size(), qm, qc, CL, arena, ws, h->wsd.as<double>(), d_segs,
+                                 rank, eps, h->opts.max_rank, h->st);
       });
     }
     if (!sk.empty())
       timed_lv(h, "sketch", level, 1, [&] {
         Launch<real>::sketch(reinterpret_cast<const SketchTask*>(d + o_sk), (int)sk.size(), maxm,
-                             maxl, arena, ws, d_gptr, d_gstr, h->st);
+                             maxl, arena, ws, d_segs, h->st);
       });
     long long* dbg = nullptr;
     if (h->profiling && h->profile_levels) {
@@ -610,7 +626,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     }
     timed_lv(h, "prep", level, 1, [&] {
       Launch<real>::prep(d_prep, nt, arena, fac, ws,
-                         h->wsd.as<double>(), d_gptr, d_gstr, rank, eps, sym ? 1 : 0,
+                         h->wsd.as<double>(), d_segs, rank, eps, sym ? 1 : 0,
                          h->opts.max_rank, maxm, h->d_err.as<DevError>(), level, dbg, h->st);
     });
     if (dbg) {
@@ -633,17 +649,17 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     }
     timed_lv(h, "gemm_coarse", level, sym ? 1 : 2, [&] {
       Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gY), (int)gY.size(), maxm,
-                                maxnw, fac, fac, arena, d_gptr, d_gstr, rank, h->st);
+                                maxnw, fac, fac, arena, d_segs, rank, h->st);
       if (!sym)
         Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gXT), (int)gXT.size(),
-                                  maxm, maxnw, fac, fac, arena, d_gptr, d_gstr, rank, h->st);
+                                  maxm, maxnw, fac, fac, arena, d_segs, rank, h->st);
     });
     timed_lv(h, "gemm_fill", level, sym ? 1 : 2, [&] {
       Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gE), (int)gE.size(), maxm,
-                                maxnwf, ws, ws, arena, d_gptr, d_gstr, rank, h->st);
+                                maxnwf, ws, ws, arena, d_segs, rank, h->st);
       if (!sym)
         Launch<real>::gemm_gather(reinterpret_cast<const GemmTask*>(d + o_gE2), (int)gE2.size(),
-                                  maxm, maxnwf, ws, ws, arena, d_gptr, d_gstr, rank, h->st);
+                                  maxm, maxnwf, ws, ws, arena, d_segs, rank, h->st);
     });
     timed_lv(h, "scatter", level, 2, [&] {
       Launch<real>::scatter(reinterpret_cast<const ScatterSeg*>(d + o_segN), (int)segN.size(),
@@ -653,7 +669,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     });
     timed_lv(h, "schur", level, 1, [&] {
       Launch<real>::schur(reinterpret_cast<const SchurTask*>(d + o_sch), (int)sch.size(), maxnw,
-                          fac, arena, reinterpret_cast<const int*>(d + o_smap),
+                          fac, arena, d_segs,
                           reinterpret_cast<const int64_t*>(d + o_sbase),
                           reinterpret_cast<const int*>(d + o_sld), rank, h->st);
     });

@@ -515,7 +515,7 @@ template <typename real>
 __global__ void __launch_bounds__(kPrepThreads)
 prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* __restrict__ fac,
             real* __restrict__ ws_all, double* __restrict__ wsd_all,
-            const int64_t* __restrict__ gptr, const int* __restrict__ gstr, int* rank,
+            const Seg* __restrict__ segs, int* rank,
             double eps, double noise_rtol, int sym, int max_rank, int smem_mats, int smem_m,
             DevError* err, int level, long long* dbg) {
   __shared__ double red_d[kPrepThreads];
@@ -587,8 +587,9 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
     const int nc = tk.ncolG;
     // flag nonzero columns: one thread per column, batched independent loads
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
-      const int64_t p = gptr[tk.gcol + q];
-      const int st = gstr[tk.gcol + q];
+      int64_t p;
+      int st;
+      seg_col(segs + tk.gcol, tk.ngcol, q, &p, &st);
       bool nz = false;
       for (int i = 0; i < m; i += 8) {
         real x[8];
@@ -626,8 +627,9 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
       const int d = (int)orig[q];
       if (d < 0) continue;
-      const int64_t p = gptr[tk.gcol + q];
-      const int st = gstr[tk.gcol + q];
+      int64_t p;
+      int st;
+      seg_col(segs + tk.gcol, tk.ngcol, q, &p, &st);
       for (int i = 0; i < m; i += 8) {
         real x[8];
 #pragma unroll
@@ -796,7 +798,7 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
 
 template <typename real>
 void Launch<real>::prep(const PrepTask* tasks_dev, int ntask, real* arena, real* fac, real* ws,
-                        double* wsd, const int64_t* gptr, const int* gstr, int* rank, double eps,
+                        double* wsd, const Seg* segs, int* rank, double eps,
                         int sym, int max_rank, int maxm, DevError* err, int level,
                         long long* dbg, cudaStream_t st) {
   if (ntask <= 0) return;
@@ -815,7 +817,7 @@ void Launch<real>::prep(const PrepTask* tasks_dev, int ntask, real* arena, real*
   cudaFuncSetAttribute(prep_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)std::max<size_t>(smem, 48 * 1024));
   count_launch();
-  prep_kernel<real><<<ntask, kPrepThreads, smem, st>>>(tasks_dev, arena, fac, ws, wsd, gptr, gstr,
+  prep_kernel<real><<<ntask, kPrepThreads, smem, st>>>(tasks_dev, arena, fac, ws, wsd, segs,
                                                         rank, eps, noise_rtol, sym, max_rank, mats,
                                                         maxm, err, level, dbg);
 }

@@ -35,8 +35,7 @@ template <typename real>
 __global__ void __launch_bounds__(256)
 gemm_gather_kernel(const GemmTask* __restrict__ tasks, const real* __restrict__ Abase,
                    real* __restrict__ Cbase, const real* __restrict__ Bbase,
-                   const int64_t* __restrict__ bptr, const int* __restrict__ bstr,
-                   const int* __restrict__ rank) {
+                   const Seg* __restrict__ segs, const int* __restrict__ rank) {
   const GemmTask tk = tasks[blockIdx.z];
   const int r = rank[tk.s];
   int M = tk.M;
@@ -51,6 +50,12 @@ gemm_gather_kernel(const GemmTask* __restrict__ tasks, const real* __restrict__ 
   if (i0 >= M || j0 >= N) return;
   __shared__ real As[TK][TM + 1];
   __shared__ real Bs[TK][TN + 1];
+  __shared__ int64_t cp[TN];
+  __shared__ int cst[TN];
+  // this tile's gathered columns: offset and stride, resolved once
+  if (threadIdx.x < TN && j0 + threadIdx.x < tk.N)
+    seg_col(segs + tk.bcol, tk.nseg, j0 + threadIdx.x, &cp[threadIdx.x], &cst[threadIdx.x]);
+  __syncthreads();
   const real* A = Abase + tk.A;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   real acc[4][4];
@@ -70,10 +75,7 @@ gemm_gather_kernel(const GemmTask* __restrict__ tasks, const real* __restrict__ 
       int l = e % TK, j = e / TK;
       int gl = l0 + l, gj = j0 + j;
       real v = 0;
-      if (gl < K && gj < N) {
-        int64_t p = bptr[tk.bcol + gj];
-        v = Bbase[p + (int64_t)gl * bstr[tk.bcol + gj]];
-      }
+      if (gl < K && gj < N) v = Bbase[cp[j] + (int64_t)gl * cst[j]];
       Bs[l][j] = v;
     }
     __syncthreads();
@@ -118,8 +120,7 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 template <typename real>
 __global__ void __launch_bounds__(256)
 sketch_kernel(const SketchTask* __restrict__ tasks, const real* __restrict__ arena,
-              real* __restrict__ ws, const int64_t* __restrict__ gptr,
-              const int* __restrict__ gstr) {
+              real* __restrict__ ws, const Seg* __restrict__ segs) {
   const SketchTask tk = tasks[blockIdx.z];
   const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
   if (i0 >= tk.m || j0 >= tk.l) return;
@@ -132,13 +133,17 @@ sketch_kernel(const SketchTask* __restrict__ tasks, const real* __restrict__ are
   for (int a = 0; a < 4; a++)
 #pragma unroll
     for (int b = 0; b < 4; b++) acc[a][b] = 0;
+  __shared__ int64_t cp[TK];
+  __shared__ int cst[TK];
   for (int q0 = 0; q0 < tk.ncol; q0 += TK) {
+    if (threadIdx.x < TK && q0 + threadIdx.x < tk.ncol)
+      seg_col(segs + tk.gcol, tk.nseg, q0 + threadIdx.x, &cp[threadIdx.x], &cst[threadIdx.x]);
+    __syncthreads();
     for (int e = threadIdx.x; e < TM * TK; e += 256) {
       int i = e % TM, l = e / TM;
       int gi = i0 + i, q = q0 + l;
       real v = 0;
-      if (gi < tk.m && q < tk.ncol)
-        v = arena[gptr[tk.gcol + q] + (int64_t)gi * gstr[tk.gcol + q]];
+      if (gi < tk.m && q < tk.ncol) v = arena[cp[l] + (int64_t)gi * cst[l]];
       As[l][i] = v;
     }
     for (int e = threadIdx.x; e < TK * TN; e += 256) {
@@ -181,7 +186,7 @@ sketch_kernel(const SketchTask* __restrict__ tasks, const real* __restrict__ are
 template <typename real>
 __global__ void __launch_bounds__(256)
 schur_kernel(const SchurTask* __restrict__ tasks, const real* __restrict__ fac,
-             real* __restrict__ arena, const int* __restrict__ map,
+             real* __restrict__ arena, const Seg* __restrict__ segs,
              const int64_t* __restrict__ base, const int* __restrict__ ldn,
              const int* __restrict__ rank) {
   const SchurTask tk = tasks[blockIdx.z];
@@ -229,23 +234,45 @@ schur_kernel(const SchurTask* __restrict__ tasks, const real* __restrict__ fac,
     }
     __syncthreads();
   }
-  const int* mp = map + tk.map;
+  // neighbour (run) and local index of every row/column of the tile: the
+  // runs of a cluster's neighbour columns, one per neighbour
+  __shared__ int rblk[TM], rloc[TM], cblk[TN], cloc[TN];
+  const Seg* sg = segs + tk.map;
+  for (int e = threadIdx.x; e < TM + TN; e += blockDim.x) {
+    const int r = (e < TM) ? i0 + e : j0 + (e - TM);
+    int a = 0, lr = 0;
+    if (r < N) {
+      int lo = 0, hi = tk.nb - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sg[mid].colstart <= r) lo = mid;
+        else hi = mid - 1;
+      }
+      a = lo;
+      lr = r - sg[lo].colstart;
+    }
+    if (e < TM) {
+      rblk[e] = a;
+      rloc[e] = lr;
+    } else {
+      cblk[e - TM] = a;
+      cloc[e - TM] = lr;
+    }
+  }
+  __syncthreads();
   const int64_t* bs = base + tk.base;
   const int* ldv = ldn + tk.ldn;
 #pragma unroll
   for (int p = 0; p < 4; p++) {
-    int gi = i0 + ty + 16 * p;
+    const int ii = ty + 16 * p, gi = i0 + ii;
     if (gi >= N) continue;
-    int rm = mp[gi];
-    int a = rm >> 20, lr = rm & 0xFFFFF;
-    int64_t lda = ldv[a];
+    const int a = rblk[ii], lr = rloc[ii];
+    const int64_t lda = ldv[a];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-      int gj = j0 + tx + 16 * q;
+      const int jj = tx + 16 * q, gj = j0 + jj;
       if (gj >= N) continue;
-      int cm = mp[gj];
-      int b = cm >> 20, lc = cm & 0xFFFFF;
-      int64_t addr = bs[a * tk.nb + b] + lr + lc * lda;
+      const int64_t addr = bs[a * tk.nb + cblk[jj]] + lr + cloc[jj] * lda;
       arena[addr] -= acc[p][q];
     }
   }
@@ -425,38 +452,37 @@ __global__ void axpby_kernel(int64_t n, int nrhs, const double* __restrict__ alp
 template <typename real>
 void Launch<real>::gemm_gather(const GemmTask* tasks_dev, int ntask, int maxM, int maxN,
                                const real* Abase, real* Cbase, const real* Bbase,
-                               const int64_t* bptr, const int* bstr, const int* rank,
+                               const Seg* segs, const int* rank,
                                cudaStream_t st) {
   if (ntask <= 0 || maxM <= 0 || maxN <= 0) return;
   for (int t0 = 0; t0 < ntask; t0 += kMaxGridYZ) {
     dim3 grid((maxN + TN - 1) / TN, (maxM + TM - 1) / TM, std::min(kMaxGridYZ, ntask - t0));
     count_launch();
-    gemm_gather_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, Abase, Cbase, Bbase, bptr,
-                                                    bstr, rank);
+    gemm_gather_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, Abase, Cbase, Bbase, segs,
+                                                    rank);
   }
 }
 
 template <typename real>
 void Launch<real>::sketch(const SketchTask* tasks_dev, int ntask, int maxm, int maxl,
-                          const real* arena, real* ws, const int64_t* gptr, const int* gstr,
-                          cudaStream_t st) {
+                          const real* arena, real* ws, const Seg* segs, cudaStream_t st) {
   if (ntask <= 0 || maxm <= 0 || maxl <= 0) return;
   for (int t0 = 0; t0 < ntask; t0 += kMaxGridYZ) {
     dim3 grid((maxl + TN - 1) / TN, (maxm + TM - 1) / TM, std::min(kMaxGridYZ, ntask - t0));
     count_launch();
-    sketch_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, arena, ws, gptr, gstr);
+    sketch_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, arena, ws, segs);
   }
 }
 
 template <typename real>
 void Launch<real>::schur(const SchurTask* tasks_dev, int ntask, int maxnw, const real* fac,
-                         real* arena, const int* map, const int64_t* base, const int* ldn,
+                         real* arena, const Seg* segs, const int64_t* base, const int* ldn,
                          const int* rank, cudaStream_t st) {
   if (ntask <= 0 || maxnw <= 0) return;
   for (int t0 = 0; t0 < ntask; t0 += kMaxGridYZ) {
     dim3 grid((maxnw + TN - 1) / TN, (maxnw + TM - 1) / TM, std::min(kMaxGridYZ, ntask - t0));
     count_launch();
-    schur_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, fac, arena, map, base, ldn, rank);
+    schur_kernel<real><<<grid, 256, 0, st>>>(tasks_dev + t0, fac, arena, segs, base, ldn, rank);
   }
 }
 
@@ -522,11 +548,6 @@ void Launch<real>::perm_out(const int64_t* perm, int64_t n, const real* src, int
   perm_out_kernel<real><<<grid_for(n * nrhs, 256), 256, 0, st>>>(perm, n, src, lds, dst, ldd, nrhs);
 }
 
-template <typename real>
-void Launch<real>::dense_top_factor(real*, int, int, int*, DevError*, cudaStream_t) {}
-template <typename real>
-void Launch<real>::dense_top_solve(const real*, int, int, const int*, real*, int64_t, int,
-                                   cudaStream_t) {}
 
 template struct Launch<double>;
 template struct Launch<float>;

@@ -82,7 +82,7 @@ template <typename real>
 __global__ void __launch_bounds__(256)
 qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ arena,
                   real* __restrict__ ws_all, double* __restrict__ wsd_all,
-                  const int64_t* __restrict__ gptr, const int* __restrict__ gstr, int* rank,
+                  const Seg* __restrict__ segs, int* rank,
                   double eps, double noise_rtol, int max_rank, int ldsm, int ccmax) {
   cg::cluster_group cl = cg::this_cluster();
   const int CL = (int)cl.num_blocks();
@@ -120,8 +120,9 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
   const int nq = q1 - q0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int t = warp; t < nq; t += nwarp) {
-    const int64_t p = gptr[tk.gcol + q0 + t];
-    const int st = gstr[tk.gcol + q0 + t];
+    int64_t p;
+    int st;
+    seg_col(segs + tk.gcol, tk.ngcol, q0 + t, &p, &st);
     bool nz = false;
     for (int i = lane; i < m; i += 32) nz |= (arena[p + (int64_t)i * st] != real(0));
     nz = __any_sync(0xffffffffu, nz);
@@ -138,8 +139,9 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
   for (int t = warp; t < nq; t += nwarp) {
     const int d = tpos[t];
     if (d < 0) continue;
-    const int64_t p = gptr[tk.gcol + q0 + t];
-    const int st = gstr[tk.gcol + q0 + t];
+    int64_t p;
+    int st;
+    seg_col(segs + tk.gcol, tk.ngcol, q0 + t, &p, &st);
     for (int i = lane; i < m; i += 32) Gs[i + (int64_t)d * ldsm] = arena[p + (int64_t)i * st];
     if (lane == 0) oidx[d] = q0 + t;
   }
@@ -259,8 +261,8 @@ size_t Launch<real>::qr_cluster_smem(int maxm, int maxc, int CL) {
 
 template <typename real>
 void Launch<real>::qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, int maxc, int CL,
-                              const real* arena, real* ws, double* wsd, const int64_t* gptr,
-                              const int* gstr, int* rank, double eps, int max_rank,
+                              const real* arena, real* ws, double* wsd, const Seg* segs,
+                              int* rank, double eps, int max_rank,
                               cudaStream_t st) {
   if (ntask <= 0) return;
   const double noise_rtol = sizeof(real) == 8 ? 1e-14 : 1e-6;
@@ -285,8 +287,7 @@ void Launch<real>::qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, in
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
-    cudaLaunchKernelEx(&cfg, qr_cluster_kernel<real>, tasks_dev + t0, arena, ws, wsd, gptr, gstr,
-                       rank, eps, noise_rtol, max_rank, maxm + 1, cc);
+    cudaLaunchKernelEx(&cfg, qr_cluster_kernel<real>, tasks_dev + t0, arena, ws, wsd, segs, rank, eps, noise_rtol, max_rank, maxm + 1, cc);
   }
 }
 

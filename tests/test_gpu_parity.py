@@ -267,3 +267,29 @@ def test_cluster_qr_equals_single_cta(hs, precision):
     assert ranks[0] == ranks[1]
     tol = 1e-12 if precision == "fp64" else 1e-5
     assert _rel(outs[1], outs[0]) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_fp32"])
+def test_dense_top_blocked(hs, precision):
+    # a top level of more than 256 unknowns goes to the blocked multi-CTA
+    # Cholesky and inverse factor (Alg. 1, dense factor when small enough);
+    # sizes not multiples of the 64-wide panels
+    p = I.poisson((16, 16, 16))
+    fac = _oracle(p, 64, 1e-2, top_size=2000)
+    assert any(lv.top is not None and lv.top["n"] > 256 for lv in fac.levels)
+    s = hs.Solver.from_problem(p, leaf_size=64, symmetric=1, top_size=2000)
+    s.factor(1e-2, precision)
+    top = max(lv.top["n"] for lv in fac.levels if lv.top is not None)
+    if precision == "fp64":
+        assert s.stats()["top_size"] == top
+    else:  # float32 blocks may decide a rank differently near the threshold
+        assert abs(s.stats()["top_size"] - top) <= 0.02 * top
+    b = I.rhs(p.n, 2, seed=41)
+    ref = H.solve(fac, b.T).T
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out, ref) < (1e-10 if precision == "fp64" else 2e-3), _rel(out, ref)
+    x, info = s.solve(torch.from_numpy(b).cuda(), krylov="pcg", tol=1e-10)
+    xx = x.cpu().numpy()
+    for c in range(2):
+        assert np.linalg.norm(b[c] - p.scipy() @ xx[c]) <= 1.0001e-10 * np.linalg.norm(b[c])
+    s.close()
