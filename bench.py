@@ -259,6 +259,21 @@ def run_gpu(args, rank, world):
     return res
 
 
+def aggregate_replicas(res: dict, device: str = "cpu") -> dict:
+    """Replicas only (the method does not shard): every rank factors and
+    solves its own copy; the job's latency is the slowest rank's.  Reduces
+    ms_per_step, p50 and p99 with MAX over the process group (any backend)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([res["ms_per_step"], res.get("p50_ms") or 0.0, res.get("p99_ms") or 0.0],
+                     dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    res["value"] = res["ms_per_step"] = float(t[0])
+    res["p50_ms"], res["p99_ms"] = float(t[1]), float(t[2])
+    res["n_gpus"] = dist.get_world_size()
+    return res
+
+
 def cpu_baseline(args, steps=1):
     """The float64 oracle on the host cores, on a bounded sample: the same
     problem family, leaf, eps and tolerance on a 32^3 grid (N/8), with the
@@ -336,10 +351,7 @@ def main():
     res = run_gpu(args, rank, world)
     if world > 1:
         import torch
-        import torch.distributed as dist
-        t = torch.tensor([res["ms_per_step"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        res["value"] = res["ms_per_step"] = float(t.item())
+        aggregate_replicas(res, device="cuda")
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             d, err = cpu_baseline(args, steps=1)

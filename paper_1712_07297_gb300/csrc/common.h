@@ -184,8 +184,11 @@ struct Launch {
   // does not fit), its dynamic shared memory, and the launch
   static int qr_cluster_size(int maxm, int maxc);
   static size_t qr_cluster_smem(int maxm, int maxc, int CL);
+  static void count_nz(const PrepTask* tasks_dev, int ntask, int maxc, const real* arena,
+                       double* wsd, const Seg* segs, int* cnt, cudaStream_t st);
   static void qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, int maxc, int CL,
-                         const real* arena, real* ws, double* wsd, const Seg* segs, int* rank, double eps, int max_rank, cudaStream_t st);
+                         const real* arena, real* ws, double* wsd, const Seg* segs, int* rank,
+                         const int* cnt, double eps, int max_rank, cudaStream_t st);
   static void sketch(const SketchTask* tasks_dev, int ntask, int maxm, int maxl,
                      const real* arena, real* ws, const Seg* segs,
                      cudaStream_t st);

@@ -185,8 +185,8 @@ struct hsolve_handle {
   int64_t coarse_total = 0;
   // scratch
   DevBuf d_err;
-  DevBuf ws, wsd, blob_dev, blob2;
-  PinnedBuf pin, pin2;
+  DevBuf ws, wsd, blob_dev, blob2, blob3, cnt;
+  PinnedBuf pin, pin2, pin3;
   // CUDA graphs of the substitution sweeps, one per nrhs (dropped whenever
   // the factorization or the level buffers change)
   bool use_graphs = true;
@@ -584,34 +584,53 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     // shared memory) for every cluster that neither sketches nor has no fill
     std::vector<PrepTask> qrt;
     int qm = 0, qc = 0;
-    if (h->opts.cluster_qr) {
+    if (h->opts.cluster_qr)
       for (auto& pt : prep)
         if (pt.l == 0 && pt.ncolG > 0) {
           qm = std::max(qm, pt.m);
           qc = std::max(qc, pt.ncolG);
-        }
-    }
-    const int CL = qm > 0 ? Launch<real>::qr_cluster_size(qm, qc) : 0;
-    if (CL > 0)
-      for (auto& pt : prep)
-        if (pt.l == 0 && pt.ncolG > 0) {
-          pt.qr = 2;
-          qrt.push_back(pt);
+          PrepTask q = pt;
+          q.qr = 2;
+          qrt.push_back(q);
         }
     if (!qrt.empty()) {
-      // the prep tasks changed (qr = 2): upload them again with the QR tasks
+      // count the nonzero fill columns on the device; the cluster size and
+      // shared memory follow the largest compacted block
       Blob b2;
-      size_t o2_prep = b2.add(prep), o2_qr = b2.add(qrt);
+      size_t o2_qr = b2.add(qrt);
       h->blob2.ensure(std::max<size_t>(b2.h.size(), 16));
       h->pin2.ensure(std::max<size_t>(b2.h.size(), 16));
       std::memcpy(h->pin2.p, b2.h.data(), b2.h.size());
       HS_CUDA(cudaMemcpyAsync(h->blob2.p, h->pin2.p, b2.h.size(), cudaMemcpyHostToDevice, h->st));
-      d_prep = reinterpret_cast<const PrepTask*>(h->blob2.as<char>() + o2_prep);
-      timed_lv(h, "qr_cluster", level, 1, [&] {
-        Launch<real>::qr_cluster(reinterpret_cast<const PrepTask*>(h->blob2.as<char>() + o2_qr),
-                                 (int)qrt.size(), qm, qc, CL, arena, ws, h->wsd.as<double>(), d_segs,
-                                 rank, eps, h->opts.max_rank, h->st);
+      const PrepTask* d_qrt = reinterpret_cast<const PrepTask*>(h->blob2.as<char>() + o2_qr);
+      h->cnt.ensure(sizeof(int) * qrt.size());
+      timed_lv(h, "count_nz", level, 1, [&] {
+        Launch<real>::count_nz(d_qrt, (int)qrt.size(), qc, arena, h->wsd.as<double>(), d_segs,
+                               h->cnt.as<int>(), h->st);
       });
+      std::vector<int> cnt(qrt.size());
+      HS_CUDA(cudaMemcpyAsync(cnt.data(), h->cnt.p, sizeof(int) * cnt.size(),
+                              cudaMemcpyDeviceToHost, h->st));
+      HS_CUDA(cudaStreamSynchronize(h->st));
+      const int nzmax = std::max(1, *std::max_element(cnt.begin(), cnt.end()));
+      const int CL = Launch<real>::qr_cluster_size(qm, nzmax);
+      if (CL > 0) {
+        for (auto& pt : prep)
+          if (pt.l == 0 && pt.ncolG > 0) pt.qr = 2;
+        Blob b3;
+        size_t o3_prep = b3.add(prep);
+        h->blob3.ensure(std::max<size_t>(b3.h.size(), 16));
+        h->pin3.ensure(std::max<size_t>(b3.h.size(), 16));
+        std::memcpy(h->pin3.p, b3.h.data(), b3.h.size());
+        HS_CUDA(cudaMemcpyAsync(h->blob3.p, h->pin3.p, b3.h.size(), cudaMemcpyHostToDevice,
+                                h->st));
+        d_prep = reinterpret_cast<const PrepTask*>(h->blob3.as<char>() + o3_prep);
+        timed_lv(h, "qr_cluster", level, 1, [&] {
+          Launch<real>::qr_cluster(d_qrt, (int)qrt.size(), qm, nzmax, CL, arena, ws,
+                                   h->wsd.as<double>(), d_segs, rank, h->cnt.as<int>(), eps,
+                                   h->opts.max_rank, h->st);
+        });
+      }
     }
     if (!sk.empty())
       timed_lv(h, "sketch", level, 1, [&] {

@@ -538,12 +538,18 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
   const int64_t mm = (int64_t)m * m;
   real* ws = ws_all + tk.ws;
   real* smat = reinterpret_cast<real*>(dsm);
-  real* vsh = smat + (int64_t)smem_mats * smem_m * smem_m;  // m reals
+  real* vsh = smat + (int64_t)smem_mats * (smem_m | 1) * smem_m;  // m reals
   real* tsh = vsh + smem_m;                                  // m reals
-  real* W_A = smem_mats >= 1 ? smat : ws;                               // A_ss -> factor -> inverse factor
-  real* W_B = smem_mats >= 2 ? smat + (int64_t)smem_m * smem_m : ws + mm;  // A_ss^{-1}
+  // shared-memory matrices get an odd leading dimension: loops that give one
+  // column to each thread then touch 32 different banks
+  const int64_t reg = (int64_t)(smem_m | 1) * smem_m;  // one shared region
+  const int ldA = smem_mats >= 1 ? (m | 1) : m;
+  const int ldB = smem_mats >= 2 ? (m | 1) : m;
+  const int ldU = smem_mats >= 3 ? (m | 1) : m;
+  real* W_A = smem_mats >= 1 ? smat : ws;                  // A_ss -> factor -> inverse factor
+  real* W_B = smem_mats >= 2 ? smat + reg : ws + mm;       // A_ss^{-1}
   // [U V_L] as one m x m matrix: U in columns 0..k, V_L in columns k..m
-  real* W_U = smem_mats >= 3 ? smat + 2 * (int64_t)smem_m * smem_m : ws + 2 * mm;
+  real* W_U = smem_mats >= 3 ? smat + 2 * reg : ws + 2 * mm;
   real* W_X = ws + 3 * mm;   // X = B U, then its reflectors
   real* W_V = W_U + (int64_t)0;  // V_L = columns k..m of W_U (set below)
   real* W_T = ws + 4 * mm;   // [U V_L]^T B
@@ -562,16 +568,17 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
   real* T = fac + tk.T;
 
   // ---- A_ss, its largest magnitude (scale of the noise floor), its factor
-  cta_copy<real>(m, m, arena + tk.a_ss, tk.ld, W_A, m);
+  cta_copy<real>(m, m, arena + tk.a_ss, tk.ld, W_A, ldA);
   {
     double mx = 0;
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) mx = fmax(mx, fabs((double)W_A[idx]));
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x)
+      mx = fmax(mx, fabs((double)W_A[idx % m + (int64_t)(idx / m) * ldA]));
     mx = cta_max_d(mx, red_d);
     if (threadIdx.x == 0) s_amax = mx;
     __syncthreads();
   }
-  const bool ok = sym ? cta_cholesky<real>(m, W_A, m, &sflag)
-                      : cta_lu<real>(m, W_A, m, piv, red_d, red_i, &sflag);
+  const bool ok = sym ? cta_cholesky<real>(m, W_A, ldA, &sflag)
+                      : cta_lu<real>(m, W_A, ldA, piv, red_d, red_i, &sflag);
   if (!ok) {
     report<real>(err, sym ? (int)HSOLVE_ERR_NOT_SPD : (int)HSOLVE_ERR_SINGULAR, tk.s, level, rank, m);
     return;
@@ -653,11 +660,13 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
     // the not yet used A_ss^{-1} and [U V] buffers when it fits; the kept
     // reflectors then move to W_G (column-major, ld m) for U
     real* Ysrc = ws_all + tk.Y;
-    real* Yq = (smem_mats >= 3 && (int64_t)m * tk.l <= 2 * (int64_t)smem_m * smem_m) ? W_B : Ysrc;
-    if (Yq != Ysrc) cta_copy<real>(m, tk.l, Ysrc, m, Yq, m);
-    k = cta_householder_qr<real, false>(m, tk.l, Yq, m, nrm2, orig, tau, true, eps, kmax,
+    const bool ysm = smem_mats >= 3 && (int64_t)(m | 1) * tk.l <= 2 * reg;
+    real* Yq = ysm ? W_B : Ysrc;
+    const int ldY = ysm ? (m | 1) : m;
+    if (ysm) cta_copy<real>(m, tk.l, Ysrc, m, Yq, ldY);
+    k = cta_householder_qr<real, false>(m, tk.l, Yq, ldY, nrm2, orig, tau, true, eps, kmax,
                                         noise_rtol * s_amax, red_d, red_i, vsh, rsign);
-    cta_copy<real>(m, k, Yq, m, W_G, m);
+    cta_copy<real>(m, k, Yq, ldY, W_G, m);
   } else if (ncol > 0) {
     k = cta_householder_qr<real, true>(m, ncol, W_G, ncol, nrm2, orig, tau, true, eps, kmax,
                                        noise_rtol * s_amax, red_d, red_i, vsh, rsign);
@@ -670,17 +679,17 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
 
   if (sym) {
     // L^{-1} in place (lower), then B = L^{-T} L^{-1}
-    cta_trtri_lower<real>(m, W_A, m, false, tsh);
-    cta_zero_tri<real>(m, W_A, m, true);
+    cta_trtri_lower<real>(m, W_A, ldA, false, tsh);
+    cta_zero_tri<real>(m, W_A, ldA, true);
     if (k == 0) {  // E_s = I: T' = L^{-1}
-      cta_copy<real>(m, m, W_A, m, T, m);
+      cta_copy<real>(m, m, W_A, ldA, T, m);
       return;
     }
-    cta_gemm<real>(m, m, m, W_A, m, true, W_A, m, false, W_B, m, real(1), real(0), gsh);
+    cta_gemm<real>(m, m, m, W_A, ldA, true, W_A, ldA, false, W_B, ldB, real(1), real(0), gsh);
   } else {
     // L^{-1} (unit lower) into W_L, U^{-1} into W_S
-    cta_copy<real>(m, m, W_A, m, W_L, m);
-    cta_copy<real>(m, m, W_A, m, W_S, m);
+    cta_copy<real>(m, m, W_A, ldA, W_L, m);
+    cta_copy<real>(m, m, W_A, ldA, W_S, m);
     cta_trtri_lower<real>(m, W_L, m, true, tsh);
     cta_zero_tri<real>(m, W_L, m, true);
     for (int i = threadIdx.x; i < m; i += blockDim.x) W_L[i + (int64_t)i * m] = real(1);
@@ -699,55 +708,61 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
     }
     // B = U^{-1} L^{-1} P
     cta_gemm<real>(m, m, m, W_S, m, false, W_L, m, false, W_F, m, real(1), real(0), gsh);
-    cta_permute_cols<real>(m, piv, W_F, m, W_B, m);
+    cta_permute_cols<real>(m, piv, W_F, m, W_B, ldB);
   }
 
   mark(4);
   // ---- U = first k columns of Q of the pivoted QR
   if (sketched || qr_done)
-    cta_form_q<real, false>(m, k, W_G, m, tau, 0, k, W_U, m, vsh);
+    cta_form_q<real, false>(m, k, W_G, m, tau, 0, k, W_U, ldU, vsh);
   else
-    cta_form_q<real, true>(m, k, W_G, ncol, tau, 0, k, W_U, m, vsh);
+    cta_form_q<real, true>(m, k, W_G, ncol, tau, 0, k, W_U, ldU, vsh);
   // orient U so that R has a positive diagonal (Gram-Schmidt directions)
   for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x) {
     int i = idx % m, j = idx / m;
-    W_U[i + (int64_t)j * m] *= rsign[j];
+    W_U[i + (int64_t)j * ldU] *= rsign[j];
   }
   __syncthreads();
 
   // ---- V_L: complement of X = B U (full QR of X, V = Q[:, k:]); in the SPD
   // case X takes the (spent) shared-memory home of the factor of A_ss
-  if (sym) W_X = W_A;
-  cta_gemm<real>(m, k, m, W_B, m, false, W_U, m, false, W_X, m, real(1), real(0), gsh);
-  cta_householder_qr<real, false>(m, k, W_X, m, nrm2, orig, tau2, false, 0.0, k, 0.0, red_d,
+  int ldX = m;
+  if (sym) {
+    W_X = W_A;
+    ldX = ldA;
+  }
+  cta_gemm<real>(m, k, m, W_B, ldB, false, W_U, ldU, false, W_X, ldX, real(1), real(0), gsh);
+  cta_householder_qr<real, false>(m, k, W_X, ldX, nrm2, orig, tau2, false, 0.0, k, 0.0, red_d,
                                   red_i, vsh);
-  W_V = W_U + (int64_t)k * m;
-  cta_form_q<real, false>(m, k, W_X, m, tau2, k, f, W_V, m, vsh);
+  W_V = W_U + (int64_t)k * ldU;
+  cta_form_q<real, false>(m, k, W_X, ldX, tau2, k, f, W_V, ldU, vsh);
 
   mark(5);
   // ---- T = [U V_L]^T B (one product); C = U^T B U -> coarse (s,s) block
-  cta_gemm<real>(m, m, m, W_U, m, true, W_B, m, false, W_T, m, real(1), real(0), gsh);
-  cta_gemm<real>(k, k, m, W_T, m, false, W_U, m, false, W_C, m, real(1), real(0), gsh);
+  cta_gemm<real>(m, m, m, W_U, ldU, true, W_B, ldB, false, W_T, m, real(1), real(0), gsh);
+  cta_gemm<real>(k, k, m, W_T, m, false, W_U, ldU, false, W_C, m, real(1), real(0), gsh);
 
   if (sym) {
     // F = V^T B V; L_F^{-1}; T' rows k.. = L_F^{-1} V^T B.  F lives where the
     // factor of A_ss was (shared memory when it fits): that factor is spent.
     W_F = W_A;
+    const int ldF = ldA;
     mark(6);
-    cta_gemm<real>(f, f, m, W_T + k, m, false, W_V, m, false, W_F, m, real(1), real(0), gsh);
-    if (!cta_cholesky<real>(f, W_F, m, &sflag)) {
+    cta_gemm<real>(f, f, m, W_T + k, m, false, W_V, ldU, false, W_F, ldF, real(1), real(0), gsh);
+    if (!cta_cholesky<real>(f, W_F, ldF, &sflag)) {
       report<real>(err, (int)HSOLVE_ERR_NOT_SPD, tk.s, level, rank, m);
       return;
     }
-    cta_trtri_lower<real>(f, W_F, m, false, tsh);
-    cta_zero_tri<real>(f, W_F, m, true);
+    cta_trtri_lower<real>(f, W_F, ldF, false, tsh);
+    cta_zero_tri<real>(f, W_F, ldF, true);
     cta_copy<real>(k, m, W_T, m, T, m);
-    cta_gemm<real>(f, m, f, W_F, m, false, W_T + k, m, false, T + k, m, real(1), real(0), gsh);
+    cta_gemm<real>(f, m, f, W_F, ldF, false, W_T + k, m, false, T + k, m, real(1), real(0), gsh);
     // D = C U^T (k x m) for the coarse-to-far update C (U^T A_sw)
-    cta_gemm<real>(k, m, k, W_C, m, false, W_U, m, true, ws_all + tk.D, m, real(1), real(0), gsh);
+    cta_gemm<real>(k, m, k, W_C, m, false, W_U, ldU, true, ws_all + tk.D, m, real(1), real(0),
+                   gsh);
   } else {
     // V_R: complement of B^T U
-    cta_gemm<real>(m, k, m, W_B, m, true, W_U, m, false, W_X, m, real(1), real(0), gsh);
+    cta_gemm<real>(m, k, m, W_B, ldB, true, W_U, ldU, false, W_X, m, real(1), real(0), gsh);
     cta_householder_qr<real, false>(m, k, W_X, m, nrm2, orig, tau2, false, 0.0, k, 0.0, red_d,
                                     red_i, vsh);
     cta_form_q<real, false>(m, k, W_X, m, tau2, k, f, W_R, m, vsh);
@@ -780,10 +795,12 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
     cta_zero_tri<real>(f, W_F, m, false);
     cta_gemm<real>(m, f, f, W_R, m, false, W_F, m, false, W_S, m, real(1), real(0), gsh);
     real* TRt = fac + tk.TR;
-    cta_gemm<real>(k, m, m, W_U, m, true, W_B, m, true, TRt, m, real(1), real(0), gsh);
-    cta_gemm<real>(f, m, m, W_S, m, true, W_B, m, true, TRt + k, m, real(1), real(0), gsh);
-    cta_gemm<real>(k, m, k, W_C, m, false, W_U, m, true, ws_all + tk.D, m, real(1), real(0), gsh);
-    cta_gemm<real>(k, m, k, W_C, m, true, W_U, m, true, ws_all + tk.D2, m, real(1), real(0), gsh);
+    cta_gemm<real>(k, m, m, W_U, ldU, true, W_B, ldB, true, TRt, m, real(1), real(0), gsh);
+    cta_gemm<real>(f, m, m, W_S, m, true, W_B, ldB, true, TRt + k, m, real(1), real(0), gsh);
+    cta_gemm<real>(k, m, k, W_C, m, false, W_U, ldU, true, ws_all + tk.D, m, real(1), real(0),
+                   gsh);
+    cta_gemm<real>(k, m, k, W_C, m, true, W_U, ldU, true, ws_all + tk.D2, m, real(1), real(0),
+                   gsh);
   }
   // write C into the (s,s) block (coarse part); done last: A_ss was copied
   real* blk_ss = arena + tk.a_ss;
@@ -807,7 +824,7 @@ void Launch<real>::prep(const PrepTask* tasks_dev, int ntask, real* arena, real*
   const double noise_rtol = sizeof(real) == 8 ? 1e-14 : 1e-6;
   // the factor of A_ss and A_ss^{-1} in shared memory when they fit
   const size_t budget = 220 * 1024 - 2 * GK * (GT + 1) * sizeof(real) - 4 * 1024;
-  const size_t one = sizeof(real) * (size_t)maxm * maxm;
+  const size_t one = sizeof(real) * (size_t)(maxm | 1) * maxm;
   const size_t vec = sizeof(real) * 2 * (size_t)maxm;
   int mats = 0;
   if (3 * one + vec <= budget) mats = 3;

@@ -13,6 +13,10 @@
 // branches (its decisions use the same exchanged values), so the barriers
 // always match.
 //
+// A count pass first flags and counts the nonzero gathered columns, so that
+// each CTA holds an equal share of the nonzero ones and the cluster size and
+// shared memory are chosen for the compacted block.
+//
 // Outputs, in the layout the per-cluster kernel expects: the rank k in
 // rank[s], the reflectors v_j as column j of W_G (column-major, ld m, rows
 // j..m), tau_j and the sign of R's diagonal in the per-cluster double
@@ -29,6 +33,7 @@ namespace hs {
 namespace {
 
 constexpr double kTieRtol = 1e-10;
+constexpr int kMaxGrid = 1 << 20;
 
 // Dynamic shared memory of one CTA: every array starts on a 16-byte boundary
 // (the same computation sizes the launch and carves the buffer).
@@ -40,7 +45,7 @@ struct QrSmem {
     nrm = G + al((size_t)ldsm * cc * sz);
     oidx = nrm + al((size_t)cc * sizeof(double));
     tpos = oidx + al((size_t)cc * sizeof(int));
-    vbuf = tpos + al((size_t)cc * sizeof(int));
+    vbuf = tpos + al((size_t)256 * sizeof(int));
     vloc = vbuf + al((size_t)ldsm * sz);
     total = vloc + al((size_t)ldsm * sz);
   }
@@ -53,6 +58,19 @@ struct Exchange {
   int cand;        // lowest original index among the local candidates
   int loc;         // local column of the candidate
 };
+
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xffffffffu, v, o);
+    v = x < v ? x : v;
+  }
+  return v;
+}
 
 __device__ double block_max(double v, double* red) {
   red[threadIdx.x] = v;
@@ -82,7 +100,7 @@ template <typename real>
 __global__ void __launch_bounds__(256)
 qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ arena,
                   real* __restrict__ ws_all, double* __restrict__ wsd_all,
-                  const Seg* __restrict__ segs, int* rank,
+                  const Seg* __restrict__ segs, int* rank, const int* __restrict__ cnt,
                   double eps, double noise_rtol, int max_rank, int ldsm, int ccmax) {
   cg::cluster_group cl = cg::this_cluster();
   const int CL = (int)cl.num_blocks();
@@ -92,7 +110,6 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
   __shared__ double red_d[256];
   __shared__ int red_i[256];
   __shared__ Exchange xch;
-  __shared__ int s_nloc, s_loc;
   extern __shared__ __align__(16) unsigned char dsm[];
   const QrSmem lay(ldsm, ccmax, (int)sizeof(real));
   real* Gs = reinterpret_cast<real*>(dsm + lay.G);  // ldsm x ccmax, column-major
@@ -114,36 +131,45 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
     amx = fmax(amx, fabs((double)arena[tk.a_ss + idx % m + (int64_t)(idx / m) * tk.ld]));
   const double floor = noise_rtol * block_max(amx, red_d);
 
-  // this CTA's share of the gathered columns; keep the nonzero ones
-  const int cc = (c + CL - 1) / CL;
-  const int q0 = min(c, cr * cc), q1 = min(c, q0 + cc);
-  const int nq = q1 - q0;
+  // The count pass flagged the nonzero gathered columns (flags[q] != 0) and
+  // counted them (nz); CTA cr keeps nonzero columns cr*cz .. (cr+1)*cz - 1
+  // in gathered order, so every CTA holds at most cz columns.
+  const double* flags = nrm2_g + tk.ncolG;
+  const int nz = cnt[blockIdx.x / CL];
+  const int cz = (nz + CL - 1) / CL;
+  const int z0 = cr * cz, z1 = min(nz, z0 + cz);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int t = warp; t < nq; t += nwarp) {
-    int64_t p;
-    int st;
-    seg_col(segs + tk.gcol, tk.ngcol, q0 + t, &p, &st);
-    bool nz = false;
-    for (int i = lane; i < m; i += 32) nz |= (arena[p + (int64_t)i * st] != real(0));
-    nz = __any_sync(0xffffffffu, nz);
-    if (lane == 0) tpos[t] = nz ? 1 : 0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  {
+    const int per = (c + blockDim.x - 1) / blockDim.x;
+    const int a0 = min(c, (int)threadIdx.x * per), a1 = min(c, a0 + per);
     int n = 0;
-    for (int t = 0; t < nq; t++) tpos[t] = tpos[t] ? n++ : -1;
-    s_nloc = n;
+    for (int q = a0; q < a1; q++) n += (flags[q] != 0.0);
+    tpos[threadIdx.x] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int t = 0; t < (int)blockDim.x; t++) {
+        const int v = tpos[t];
+        tpos[t] = acc;
+        acc += v;
+      }
+    }
+    __syncthreads();
+    int zq = tpos[threadIdx.x];
+    // the gathered column of each of this CTA's slots
+    for (int q = a0; q < a1; q++) {
+      if (flags[q] == 0.0) continue;
+      if (zq >= z0 && zq < z1) oidx[zq - z0] = q;
+      zq++;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  const int nloc = s_nloc;
-  for (int t = warp; t < nq; t += nwarp) {
-    const int d = tpos[t];
-    if (d < 0) continue;
+  const int nloc = max(0, z1 - z0);
+  for (int d = warp; d < nloc; d += nwarp) {
     int64_t p;
     int st;
-    seg_col(segs + tk.gcol, tk.ngcol, q0 + t, &p, &st);
+    seg_col(segs + tk.gcol, tk.ngcol, oidx[d], &p, &st);
     for (int i = lane; i < m; i += 32) Gs[i + (int64_t)d * ldsm] = arena[p + (int64_t)i * st];
-    if (lane == 0) oidx[d] = q0 + t;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
@@ -160,40 +186,63 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
   const int steps = min(m, c);
   double r11 = 0;
   int k = 0;
+  __shared__ unsigned long long red_u[8];
+  __shared__ double s_M, s_r;
+  __shared__ int s_owner;
   for (int j = 0; j < steps; j++) {
     // 1. largest remaining norm over the cluster
     double lmx = 0;
     for (int t = threadIdx.x; t < nloc; t += blockDim.x) lmx = fmax(lmx, nrm[t]);
-    lmx = block_max(lmx, red_d);
-    if (threadIdx.x == 0) xch.val = lmx;
-    cl.sync();
-    double M = 0;
-    for (int rr = 0; rr < CL; rr++) M = fmax(M, cl.map_shared_rank(&xch, rr)->val);
-    if (M <= 0.0) break;
-    // 2. lowest original index among the near-maximal columns
-    int lc = INT_MAX;
-    for (int t = threadIdx.x; t < nloc; t += blockDim.x)
-      if (nrm[t] >= (1.0 - kTieRtol) * M && oidx[t] < lc) lc = oidx[t];
-    lc = block_min(lc, red_i);
-    if (lc != INT_MAX)
-      for (int t = threadIdx.x; t < nloc; t += blockDim.x)
-        if (oidx[t] == lc) s_loc = t;
+    lmx = warp_max(lmx);
+    if (lane == 0) red_d[warp] = lmx;
     __syncthreads();
     if (threadIdx.x == 0) {
-      xch.cand = lc;
-      xch.loc = (lc != INT_MAX) ? s_loc : -1;
-      xch.candnrm = (lc != INT_MAX) ? nrm[s_loc] : -1.0;
+      double v = red_d[0];
+      for (int w = 1; w < nwarp; w++) v = fmax(v, red_d[w]);
+      xch.val = v;
     }
     cl.sync();
-    int best = INT_MAX, owner = 0;
-    for (int rr = 0; rr < CL; rr++) {
-      const int x = cl.map_shared_rank(&xch, rr)->cand;
-      if (x < best) {
-        best = x;
-        owner = rr;
+    if (warp == 0) {
+      double v = (lane < CL) ? cl.map_shared_rank(&xch, lane)->val : 0.0;
+      v = warp_max(v);
+      if (lane == 0) s_M = v;
+    }
+    __syncthreads();
+    const double M = s_M;
+    if (M <= 0.0) break;
+    // 2. lowest original index among the near-maximal columns: one key
+    //    (original index, local slot) per candidate, the smallest wins
+    unsigned long long key = ~0ull;
+    for (int t = threadIdx.x; t < nloc; t += blockDim.x)
+      if (nrm[t] >= (1.0 - kTieRtol) * M) {
+        const unsigned long long kk = ((unsigned long long)oidx[t] << 32) | (unsigned)t;
+        key = kk < key ? kk : key;
+      }
+    key = warp_min_u64(key);
+    if (lane == 0) red_u[warp] = key;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long v = red_u[0];
+      for (int w = 1; w < nwarp; w++) v = red_u[w] < v ? red_u[w] : v;
+      const bool any = v != ~0ull;
+      xch.cand = any ? (int)(v >> 32) : INT_MAX;
+      xch.loc = any ? (int)(v & 0xffffffffu) : -1;
+      xch.candnrm = any ? nrm[(int)(v & 0xffffffffu)] : -1.0;
+    }
+    cl.sync();
+    if (warp == 0) {
+      unsigned long long v = ~0ull;
+      if (lane < CL)
+        v = ((unsigned long long)(unsigned)cl.map_shared_rank(&xch, lane)->cand << 8) | lane;
+      v = warp_min_u64(v);
+      if (lane == 0) {
+        s_owner = (int)(v & 0xff);
+        s_r = sqrt(cl.map_shared_rank(&xch, (int)(v & 0xff))->candnrm);
       }
     }
-    const double r = sqrt(cl.map_shared_rank(&xch, owner)->candnrm);
+    __syncthreads();
+    const int owner = s_owner;
+    const double r = s_r;
     if (j == 0) r11 = r;
     if (r <= floor || (eps > 0.0 && r <= eps * r11) || j >= kmax) break;
     // 3. the owner forms the reflector v = x - beta e1, beta = -sign(x0) ||x||
@@ -243,7 +292,60 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
   cl.sync();
 }
 
+// Count pass: flag the nonzero gathered columns of every task (flags in the
+// task's double workspace after the norms) and count them.  Grid (task,
+// chunk of 256 columns), one thread per column with eight loads in flight;
+// the counts are accumulated atomically into cnt (zeroed by the caller).
+template <typename real>
+__global__ void __launch_bounds__(256)
+count_nz_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ arena,
+                double* __restrict__ wsd_all, const Seg* __restrict__ segs, int* cnt) {
+  const PrepTask tk = tasks[blockIdx.x];
+  double* flags = wsd_all + tk.wsd + tk.ncolG;
+  __shared__ int red[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  int n = 0;
+  for (int q = blockIdx.y * blockDim.x + threadIdx.x; q < tk.ncolG;
+       q += gridDim.y * blockDim.x) {
+    int64_t p;
+    int st;
+    seg_col(segs + tk.gcol, tk.ngcol, q, &p, &st);
+    bool nz = false;
+    for (int i = 0; i < tk.m; i += 8) {
+      real x[8];
+#pragma unroll
+      for (int r = 0; r < 8; r++) x[r] = (i + r < tk.m) ? arena[p + (int64_t)(i + r) * st] : real(0);
+#pragma unroll
+      for (int r = 0; r < 8; r++) nz |= (x[r] != real(0));
+    }
+    flags[q] = nz ? 1.0 : 0.0;
+    n += nz;
+  }
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if (lane == 0) red[warp] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < nwarp; w++) t += red[w];
+    if (t) atomicAdd(cnt + blockIdx.x, t);
+  }
+}
+
 }  // namespace
+
+template <typename real>
+void Launch<real>::count_nz(const PrepTask* tasks_dev, int ntask, int maxc, const real* arena,
+                            double* wsd, const Seg* segs, int* cnt, cudaStream_t st) {
+  if (ntask <= 0) return;
+  cudaMemsetAsync(cnt, 0, sizeof(int) * ntask, st);
+  const int chunks = std::max(1, std::min((maxc + 255) / 256, 64));
+  for (int t0 = 0; t0 < ntask; t0 += kMaxGrid) {
+    const int nt = std::min(kMaxGrid, ntask - t0);
+    count_launch();
+    count_nz_kernel<real><<<dim3(nt, chunks), 256, 0, st>>>(tasks_dev + t0, arena, wsd, segs,
+                                                            cnt + t0);
+  }
+}
 
 template <typename real>
 int Launch<real>::qr_cluster_size(int maxm, int maxc) {
@@ -256,13 +358,13 @@ int Launch<real>::qr_cluster_size(int maxm, int maxc) {
 template <typename real>
 size_t Launch<real>::qr_cluster_smem(int maxm, int maxc, int CL) {
   const int cc = (maxc + CL - 1) / CL;
-  return QrSmem(maxm + 1, cc, (int)sizeof(real)).total;
+  return QrSmem((maxm + 1) | 1, cc, (int)sizeof(real)).total;
 }
 
 template <typename real>
 void Launch<real>::qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, int maxc, int CL,
                               const real* arena, real* ws, double* wsd, const Seg* segs,
-                              int* rank, double eps, int max_rank,
+                              int* rank, const int* cnt, double eps, int max_rank,
                               cudaStream_t st) {
   if (ntask <= 0) return;
   const double noise_rtol = sizeof(real) == 8 ? 1e-14 : 1e-6;
@@ -287,7 +389,8 @@ void Launch<real>::qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, in
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
-    cudaLaunchKernelEx(&cfg, qr_cluster_kernel<real>, tasks_dev + t0, arena, ws, wsd, segs, rank, eps, noise_rtol, max_rank, maxm + 1, cc);
+    cudaLaunchKernelEx(&cfg, qr_cluster_kernel<real>, tasks_dev + t0, arena, ws, wsd, segs, rank,
+                       cnt + t0, eps, noise_rtol, max_rank, (maxm + 1) | 1, cc);
   }
 }
 

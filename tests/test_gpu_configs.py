@@ -1,0 +1,107 @@
+"""The measured workloads at full size, through the C-ABI.
+
+The oracle cannot factor these sizes in test time, so the checks are
+properties that hold at any size: the float64 Krylov solve reaches the
+stated relative residual (recomputed here with scipy in float64), the
+preconditioner of an SPD matrix is symmetric positive definite (x^T M^{-1} x
+> 0 and (M^{-1}u, v) = (u, M^{-1}v) on random vectors), ranks never exceed
+cluster sizes, and a smaller eps gives fewer iterations (Sec. 5.3)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1712_07297_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1712_07297_gb300 import build
+    build.build()
+    from paper_1712_07297_gb300 import hsolve
+    hsolve.load()
+    return hsolve
+
+
+def _check_residual(p, b, x, tol):
+    A = p.scipy()
+    for c in range(b.shape[0]):
+        r = np.linalg.norm(b[c] - A @ x[c]) / np.linalg.norm(b[c])
+        assert r <= tol * 1.0001, (c, r)
+
+
+def _check_spd_preconditioner(s, n, seed=0):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    u = torch.rand((2, n), generator=g, dtype=torch.float64).cuda() - 0.5
+    mu = s.apply(u).cpu().numpy()
+    uu = u.cpu().numpy()
+    assert uu[0] @ mu[0] > 0 and uu[1] @ mu[1] > 0
+    a, b = uu[0] @ mu[1], uu[1] @ mu[0]
+    assert abs(a - b) <= 1e-5 * max(abs(a), abs(b))
+
+
+def _ranks_bounded(s):
+    for l in range(s.stats()["levels"]):
+        sizes, ranks, _ = s.level(l)
+        assert np.all(ranks <= sizes) and np.all(ranks >= 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_fp32"])
+def test_poisson3d_64(hs, precision):
+    # 3D 7-point Poisson 64^3, clusters of 128, eps in {1e-2, 1e-4}, 1 and 16 RHS
+    p, st = I.workload("poisson3d_64")
+    s = hs.Solver.from_problem(p, leaf_size=128, symmetric=1, top_size=8192)
+    its = []
+    for eps in (1e-2, 1e-4):
+        s.factor(eps, precision)
+        _ranks_bounded(s)
+        for nrhs in (1, 16):
+            b = I.rhs(p.n, nrhs, seed=1001)
+            x, info = s.solve(torch.from_numpy(b).cuda(), krylov="pcg", tol=1e-10)
+            _check_residual(p, b, x.cpu().numpy(), 1e-10)
+            if nrhs == 1:
+                its.append(info.iterations)
+        if eps == 1e-2:
+            _check_spd_preconditioner(s, p.n)
+    assert its[1] <= its[0]
+    s.close()
+
+
+def test_vcdiff3d_96(hs):
+    # variable-coefficient diffusion 96^3 (10^U(-3,3) cells, harmonic faces)
+    p, st = I.workload("vcdiff3d_96")
+    s = hs.Solver.from_problem(p, leaf_size=128, symmetric=1, top_size=8192)
+    s.factor(1e-2, "mixed_fp32")
+    _ranks_bounded(s)
+    b = I.rhs(p.n, 1, seed=1002)
+    x, info = s.solve(torch.from_numpy(b).cuda(), krylov="pcg", tol=1e-10, maxit=1000)
+    _check_residual(p, b, x.cpu().numpy(), 1e-10)
+    s.close()
+
+
+def test_convdiff3d_64_gmres(hs):
+    # nonsymmetric convection-diffusion 64^3, cell Peclet 10, FGMRES(50)
+    p, st = I.workload("convdiff3d_64")
+    s = hs.Solver.from_problem(p, leaf_size=128, symmetric=0, gmres_restart=50)
+    s.factor(1e-2, "mixed_fp32")
+    _ranks_bounded(s)
+    b = I.rhs(p.n, 1, seed=1002)
+    x, info = s.solve(torch.from_numpy(b).cuda(), krylov="gmres", tol=1e-10, maxit=500)
+    _check_residual(p, b, x.cpu().numpy(), 1e-10)
+    s.close()
+
+
+def test_poisson3d_128_mixed_8rhs(hs):
+    # 3D Poisson 128^3: float32 factorization, float64 FGMRES to 1e-10, 8 RHS
+    p, st = I.workload("poisson3d_128")
+    s = hs.Solver.from_problem(p, leaf_size=128, symmetric=1, top_size=8192)
+    s.factor(1e-2, "mixed_fp32")
+    _ranks_bounded(s)
+    b = I.rhs(p.n, 8, seed=1003)
+    x, info = s.solve(torch.from_numpy(b).cuda(), krylov="gmres", tol=1e-10, maxit=300)
+    _check_residual(p, b, x.cpu().numpy(), 1e-10)
+    s.close()
