@@ -6,10 +6,11 @@ preconditioned by Alg. 2) of the 3D 7-point Poisson problem on a 64^3 grid
 entries uniform in [-1, 1], to a relative residual of 1e-10.  Analysis and the
 matrix upload are outside the timed region.
 
-The JSON line reports the float64 path (`value`) and the mixed-precision path
-(`mixed`), p50/p99 over the steps, an end-to-end figure through the host-buffer
-entry point, the roofline of the dominant kernel, the CPU oracle baseline and
-the SM clocks seen while timing.
+The JSON line reports the mixed-precision path (`value`: float32
+factorization and sweeps inside float64 PCG) and the plain float64 path
+(`fp64`), p50/p99 over the steps, an end-to-end figure through the host-buffer
+entry point, the roofline of the dominant kernel and of the substitution
+sweeps, the CPU oracle baseline and the SM clocks seen while timing.
 
 `--impl reference` times the CPU oracle (float64 numpy restatement of the
 method) on the host cores instead.
@@ -114,6 +115,13 @@ def _pct(xs, q):
     return xs[i]
 
 
+def _phase_sum(acc, ph):
+    for k, (ms, nl) in ph.items():
+        a = acc.setdefault(k, [0.0, 0])
+        a[0] += ms
+        a[1] += nl
+
+
 def run_gpu(args, rank, world):
     import numpy as np
     import torch
@@ -130,7 +138,8 @@ def run_gpu(args, rank, world):
     nrhs = args.nrhs or st["nrhs"]
     stream = torch.cuda.current_stream()
     s = hsolve.Solver.from_problem(prob, leaf_size=leaf, symmetric=1 if prob.spd else 0,
-                                   top_size=args.top_size, stream=stream)
+                                   top_size=args.top_size, stream=stream,
+                                   equilibrate=st.get("equilibrate", 0))
     krylov = "pcg" if prob.spd else "gmres"
     b_host = I.rhs(prob.n, nrhs, seed=st["rhs_seed"])
     b = torch.from_numpy(b_host).cuda()
@@ -142,10 +151,14 @@ def run_gpu(args, rank, world):
         _, info = s.solve(b, x, krylov=krylov, tol=1e-10, maxit=500)
         return info
 
-    def timed_steps(prec, steps, warmup):
+    def timed_steps(prec, steps, warmup, phases):
+        """warmup untimed steps, then steps timed with CUDA events on the
+        library's stream; per-phase kernel times are recorded inside the timed
+        steps by event pairs that never synchronise (resolved afterwards)."""
         for _ in range(warmup):
             one_step(prec)
         times, infos = [], []
+        s.set_profiling(True, deferred=True)
         for _ in range(steps):
             flush.zero_()  # L2 flush between timed steps (256 MB > 129 MB L2)
             torch.cuda.synchronize()
@@ -157,101 +170,128 @@ def run_gpu(args, rank, world):
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
             infos.append(info)
+            _phase_sum(phases, s.phase_times())
+        s.set_profiling(False)
         return times, infos
 
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    phmx, ph64 = {}, {}
     launches0 = s.stats()["launches_total"]
     with ClockSampler(dev) as clk:
-        t64, i64 = timed_steps("fp64", args.steps, args.warmup)
+        tmx, imx = timed_steps(args.mixed, args.steps, args.warmup, phmx)
     launches1 = s.stats()["launches_total"]
-    torch.cuda.synchronize()
-    st64 = s.stats()
-    tmx, imx = timed_steps(args.mixed, args.steps, max(1, args.warmup // 2))
     stmx = s.stats()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    t64, i64 = timed_steps("fp64", args.steps, args.warmup, ph64)
+    st64 = s.stats()
+    torch.cuda.synchronize()
 
     # end to end through the host-buffer entry point (copies in the region)
     e2e = []
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.factor(eps, "fp64")
+        s.factor(eps, args.mixed)
         xh, info = s.solve_host(b_host, krylov=krylov, tol=1e-10, maxit=500)
         e2e.append((time.perf_counter() - t0) * 1e3)
 
-    # per-kernel durations: one extra profiled step per precision
-    s.set_profiling(True)
-    one_step("fp64")
-    ph64 = s.phase_times()
-    s.set_profiling(False)
-    s.set_profiling(True)
-    one_step(args.mixed)
-    phmx = s.phase_times()
-    s.set_profiling(False)
-    s.factor(eps, "fp64")
+    # the substitution sweeps alone (Alg. 2): HBM-bound, one graph launch each
+    s.factor(eps, args.mixed)
+    stm = s.stats()
+    u = torch.empty_like(b)
+    for _ in range(3):
+        s.apply(b, u)
+    torch.cuda.synchronize()
+    napply = 20
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(napply):
+        s.apply(b, u)
+    a1.record(stream)
+    a1.synchronize()
+    apply_ms = a0.elapsed_time(a1) / napply
 
     peaks, pk_src = _peaks()
     clocks = clk.summary()
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    dom = max((k for k in ph64 if k not in ("upload", "assemble")), key=lambda k: ph64[k][0])
-    work = {"schur": st64["schur_flops"], "prep": st64["prep_flops"],
-            "gemm_coarse": st64["gemm_flops"], "gemm_fill": st64["gemm_flops"]}
-    if "dense_top" in ph64:
-        n_top = st64["top_size"]
-        work["dense_top"] = 2.0 / 3.0 * n_top ** 3
-        work["prep"] = st64["prep_flops"] - work["dense_top"]
-    ms_dom, nl_dom = ph64[dom]
-    fl = work.get(dom, st64["factor_flops"])
+    K = max(args.steps, 1)
+    dom = max((k for k in phmx if k not in ("upload", "assemble")), key=lambda k: phmx[k][0])
+    n_top = stmx["top_size"]
+    top_flops = float(n_top) ** 3  # Cholesky n^3/3 + explicit inverse factor 2n^3/3
+    work = {"schur": stmx["schur_flops"], "qr_cluster": stmx["qr_flops"],
+            "prep": stmx["prep_flops"] - stmx["qr_flops"] - (2.0 / 3.0) * n_top ** 3,
+            "gemm_coarse": stmx["gemm_flops"], "gemm_fill": stmx["gemm_flops"],
+            "dense_top": top_flops}
+    ms_dom, nl_dom = phmx[dom][0] / K, phmx[dom][1] / K
+    fl = work.get(dom, stmx["factor_flops"])
     ach = fl / (ms_dom * 1e-3) / 1e12
-    peak = alu_peak_tflops("f64", sm_mhz)
+    peak = alu_peak_tflops("f32", sm_mhz)
     roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": None, "launches": nl_dom,
-            "ms_total": ms_dom, "peak_source": "derived (152 SM x 2 FP64 FMA/clk x SM clock)"}
+            "frac": ach / peak, "traffic": None, "launches_per_step": nl_dom,
+            "ms_per_step": ms_dom,
+            "work": "algorithmic float32 flops per step (library counters)",
+            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x median SM clock"}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ab = stm["apply_bytes"] * 1.0
+    apply_gbs = ab / (apply_ms * 1e-3) / 1e9
+    apply_roof = {"bound": "hbm", "kernel": "apply (all sweeps, one graph)", "achieved": apply_gbs,
+                  "peak": hbm, "unit": "GB/s", "frac": apply_gbs / hbm, "ms": apply_ms,
+                  "bytes": ab, "nrhs": nrhs, "peak_source": pk_src}
+
+    def per_step(ph):
+        return {k: {"ms": round(v[0] / K, 3), "launches": round(v[1] / K, 1)} for k, v in ph.items()}
 
     res = {
         "metric": METRIC,
-        "value": statistics.mean(t64),
+        "value": statistics.mean(tmx),
         "unit": "ms",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": statistics.mean(t64),
-        "p50_ms": _pct(t64, 50),
-        "p99_ms": _pct(t64, 99),
+        "ms_per_step": statistics.mean(tmx),
+        "p50_ms": _pct(tmx, 50),
+        "p99_ms": _pct(tmx, 99),
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f32+f64",
+        "dtype_note": "float32 factorization and sweeps, float64 SpMV, Krylov and rank decisions",
         "data": "synthetic",
         "config": {"workload": "3D 7-point Poisson 64^3 (N=262144), clusters of 128, eps=1e-2, "
                                "1 RHS U[-1,1], PCG to 1e-10",
                    "n": prob.n, "nnz": prob.nnz, "leaf": leaf, "eps": eps, "nrhs": nrhs,
-                   "krylov": krylov, "top_size": args.top_size,
+                   "krylov": krylov, "top_size": args.top_size, "precision": args.mixed,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "iterations": i64[-1].iterations,
-        "rel_residual": max(i.rel_residual for i in i64),
-        "factor_ms": i64[-1].factor_ms,
-        "solve_ms": i64[-1].solve_ms,
-        "mixed": {"precision": args.mixed, "ms_per_step": statistics.mean(tmx),
-                  "p50_ms": _pct(tmx, 50), "p99_ms": _pct(tmx, 99),
-                  "iterations": imx[-1].iterations,
-                  "rel_residual": max(i.rel_residual for i in imx),
-                  "factor_ms": imx[-1].factor_ms, "solve_ms": imx[-1].solve_ms},
+        "iterations": imx[-1].iterations,
+        "rel_residual": max(i.rel_residual for i in imx),
+        "factor_ms": imx[-1].factor_ms,
+        "solve_ms": imx[-1].solve_ms,
+        "fp64": {"precision": "fp64", "ms_per_step": statistics.mean(t64),
+                 "p50_ms": _pct(t64, 50), "p99_ms": _pct(t64, 99),
+                 "iterations": i64[-1].iterations,
+                 "rel_residual": max(i.rel_residual for i in i64),
+                 "factor_ms": i64[-1].factor_ms, "solve_ms": i64[-1].solve_ms},
+        "mixed_speedup_vs_fp64": statistics.mean(t64) / statistics.mean(tmx),
         "e2e": {"value": statistics.mean(e2e), "unit": "ms",
-                "h2d_bytes_per_step": 8 * prob.n * nrhs, "d2h_bytes_per_step": 8 * prob.n * nrhs},
+                "h2d_bytes_per_step": 8 * prob.n * nrhs, "d2h_bytes_per_step": 8 * prob.n * nrhs,
+                "path": "hsolve_factor + hsolve_solve_host (pinned staging inside)"},
         "gpu_launches": int((launches1 - launches0) / max(args.steps + args.warmup, 1)),
         "gpu_launches_note": "library kernels per step (factor + solve), counted by the library",
         "roofline": roof,
-        "phases_fp64": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in ph64.items()},
-        "phases_mixed": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in phmx.items()},
-        "stats": {"levels": st64["levels"], "colours_total": st64["colours_total"],
-                  "factor_bytes": st64["factor_bytes"], "apply_bytes": st64["apply_bytes"],
-                  "factor_gflop": st64["factor_flops"] / 1e9},
+        "apply_roofline": apply_roof,
+        "phases_mixed": per_step(phmx),
+        "phases_fp64": per_step(ph64),
+        "stats": {"levels": stmx["levels"], "colours_total": stmx["colours_total"],
+                  "top_size": n_top, "factor_bytes": stmx["factor_bytes"],
+                  "apply_bytes": stmx["apply_bytes"],
+                  "factor_gflop": stmx["factor_flops"] / 1e9,
+                  "fp64_factor_gflop": st64["factor_flops"] / 1e9},
         "clocks": clocks,
         "peaks_source": pk_src,
     }

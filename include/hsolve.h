@@ -82,6 +82,13 @@ typedef struct {
                              thread-block clusters (distributed shared
                              memory); 0 = one CTA per cluster; same result
                              either way; default 1 */
+  int32_t equilibrate;    /* 1 = factor S A S with S = diag(|a_ii|)^{-1/2}
+                             (1 where a_ii = 0) and apply M^{-1} = S Mh^{-1} S,
+                             Mh the factorization of S A S; keeps truncation
+                             from losing definiteness on coefficient contrasts
+                             of 1e6 (Sec. 5.1 workloads); the Krylov methods
+                             still solve A x = b.  0 = factor A itself;
+                             default 0 */
 } hsolve_opts;
 
 typedef struct {
@@ -110,6 +117,10 @@ typedef struct {
   int32_t kernel_launches;/* kernels launched by the last hsolve_factor */
   int32_t precision;      /* hsolve_precision of the last factor */
   int64_t launches_total; /* kernels launched by the library in this process */
+  double qr_flops;        /* of prep_flops: the pivoted QR of the fill blocks,
+                             4 m c k per cluster (c = nonzero fill columns
+                             where the count pass ran, else all gathered
+                             columns; k = rank) */
 } hsolve_stats;
 
 typedef struct hsolve_handle hsolve_handle;
@@ -225,7 +236,10 @@ hsolve_status hsolve_get_phase_times(const hsolve_handle* h,
 
 /* Enable (1) or disable (0) per-phase CUDA-event timing (off by default; it
  * adds a synchronisation per phase); 2 also splits every phase by level
- * (names "<phase>.L<level>"). */
+ * (names "<phase>.L<level>"); 3 records the event pairs without any
+ * synchronisation and resolves them when hsolve_get_phase_times is called
+ * (timing inside a measured region).  The times of a factorization replace
+ * those of the previous one; solves add to them. */
 hsolve_status hsolve_set_profiling(hsolve_handle* h, int on);
 
 /* Text of the last error on this handle (never NULL). */

@@ -215,10 +215,12 @@ struct Launch {
                          real* dst, int64_t ldd, int nrhs, cudaStream_t st);
   static void scatter_vec(const int64_t* idx, int64_t n, const real* src, int64_t lds,
                           real* dst, int64_t ldd, int nrhs, cudaStream_t st);
-  static void perm_in(const int64_t* perm, int64_t n, const double* src, int64_t lds,
-                      real* dst, int64_t ldd, int nrhs, cudaStream_t st);
-  static void perm_out(const int64_t* perm, int64_t n, const real* src, int64_t lds,
-                       double* dst, int64_t ldd, int nrhs, cudaStream_t st);
+  // dst[p] = S[perm[p]] src[perm[p]] and dst[perm[p]] = S[perm[p]] src[p]
+  // (S = null: no scaling)
+  static void perm_in(const int64_t* perm, const double* S, int64_t n, const double* src,
+                      int64_t lds, real* dst, int64_t ldd, int nrhs, cudaStream_t st);
+  static void perm_out(const int64_t* perm, const double* S, int64_t n, const real* src,
+                       int64_t lds, double* dst, int64_t ldd, int nrhs, cudaStream_t st);
   // Dense top of an SPD factorization: A (n x n, ld lda) is overwritten by
   // its Cholesky factor L; X (n x n, ld n) receives L^{-1}.
   static void dense_top(real* A, int64_t lda, int n, real* X, DevError* err, int level,

@@ -164,10 +164,12 @@ struct hsolve_handle {
   std::vector<int> col;
   std::vector<double> val;
   DevBuf d_rowptr, d_col, d_val;
+  DevBuf d_fval, d_scale;  // equilibrate: values of S A S, and S by original index
   int symmetric = 1;
   hsolve_opts opts{};
   cudaStream_t st = nullptr;
   std::vector<int64_t> perm;
+  std::vector<double> scale;
   DevBuf d_perm;
   LevelPattern L0;
   std::vector<std::vector<int>> adj0;
@@ -178,7 +180,7 @@ struct hsolve_handle {
   int prec = -1;
   bool factored = false;
   double factor_ms = 0;
-  double factor_flops = 0, schur_flops = 0, prep_flops = 0, gemm_flops = 0;
+  double factor_flops = 0, schur_flops = 0, prep_flops = 0, gemm_flops = 0, qr_flops = 0;
   int64_t apply_bytes = 0, factor_bytes = 0, block_bytes = 0;
   int launches = 0;
   int colours_total = 0;
@@ -197,6 +199,11 @@ struct hsolve_handle {
     graphs.clear();
   }
   ~hsolve_handle() {
+    for (auto& q : pending) {
+      cudaEventDestroy(q.a);
+      cudaEventDestroy(q.b);
+    }
+    for (auto e : event_pool) cudaEventDestroy(e);
     drop_graphs();
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
@@ -206,9 +213,26 @@ struct hsolve_handle {
   PinnedBuf pin_small;
   bool profiling = false;
   bool profile_levels = false;
+  // deferred timing: event pairs recorded without synchronising, resolved
+  // into phases when the phase times are read or the next factor starts
+  bool profile_deferred = false;
+  struct Pending {
+    std::string name;
+    int launches;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
   std::vector<PhaseTimer> phases;
   std::string err;
 };
+
+namespace {
+// the equilibration S by original index, or null when A is factored itself
+const double* hscale(const hsolve_handle* h) {
+  return h->opts.equilibrate ? h->d_scale.as<double>() : nullptr;
+}
+}  // namespace
 
 namespace {
 
@@ -284,6 +308,25 @@ void timed(hsolve_handle* h, const char* name, int launches, Fn&& fn) {
       throw Fail(HSOLVE_ERR_CUDA, std::string(name) + " launch: " + cudaGetErrorString(e));
     return;
   }
+  if (h->profile_deferred) {
+    cudaEvent_t ev[2];
+    for (auto& e : ev) {
+      if (!h->event_pool.empty()) {
+        e = h->event_pool.back();
+        h->event_pool.pop_back();
+      } else {
+        cudaEventCreate(&e);
+      }
+    }
+    cudaEventRecord(ev[0], h->st);
+    fn();
+    cudaEventRecord(ev[1], h->st);
+    cudaError_t e = cudaGetLastError();
+    h->pending.push_back({name, launches, ev[0], ev[1]});
+    if (e != cudaSuccess)
+      throw Fail(HSOLVE_ERR_CUDA, std::string(name) + " launch: " + cudaGetErrorString(e));
+    return;
+  }
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -299,6 +342,18 @@ void timed(hsolve_handle* h, const char* name, int launches, Fn&& fn) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   phase_add(h, name, ms, launches);
+}
+
+// Resolve deferred event pairs into phase times (waits for the last one).
+void resolve_pending(hsolve_handle* h) {
+  for (auto& q : h->pending) {
+    float ms = 0;
+    if (cudaEventSynchronize(q.b) == cudaSuccess && cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess)
+      phase_add(h, q.name.c_str(), ms, q.launches);
+    h->event_pool.push_back(q.a);
+    h->event_pool.push_back(q.b);
+  }
+  h->pending.clear();
 }
 
 void check_dev_error(hsolve_handle* h) {
@@ -361,7 +416,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   int* rank = d_rank.as<int>();
   std::vector<ApplyRec> recs(nc);
   std::vector<int64_t> vmap;
-  std::vector<int> fillcols(nc, 0), fillw(nc, 0);
+  std::vector<int> fillcols(nc, 0), fillw(nc, 0), nzcols(nc, -1);
   FL.cls.clear();
   // a single large SPD cluster (the dense top of Alg. 1) goes to the blocked
   // multi-CTA Cholesky and inverse factor: E_s = I, k = 0, no neighbours
@@ -612,6 +667,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       HS_CUDA(cudaMemcpyAsync(cnt.data(), h->cnt.p, sizeof(int) * cnt.size(),
                               cudaMemcpyDeviceToHost, h->st));
       HS_CUDA(cudaStreamSynchronize(h->st));
+      for (size_t i = 0; i < qrt.size(); i++) nzcols[qrt[i].s] = cnt[i];
       const int nzmax = std::max(1, *std::max_element(cnt.begin(), cnt.end()));
       const int CL = Launch<real>::qr_cluster_size(qm, nzmax);
       if (CL > 0) {
@@ -716,6 +772,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         double gf = 2.0 * mf * mf * nw * (sym ? 1 : 2) +
                     (k > 0 ? 2.0 * k * mf * fillw[s] * (sym ? 1 : 2) : 0.0);
         double sf = 2.0 * f * (double)nw * nw;
+        if (k > 0) h->qr_flops += 4.0 * mf * (nzcols[s] >= 0 ? nzcols[s] : fillcols[s]) * k;
         h->prep_flops += pf;
         h->gemm_flops += gf;
         h->schur_flops += sf;
@@ -847,11 +904,12 @@ void build_next(hsolve_handle* h, FLevel& FL, const real* arena, std::unique_ptr
 template <typename real>
 void factor_impl(hsolve_handle* h, double eps) {
   h->F.clear();
-  h->factor_flops = h->schur_flops = h->prep_flops = h->gemm_flops = 0;
+  h->factor_flops = h->schur_flops = h->prep_flops = h->gemm_flops = h->qr_flops = 0;
   h->apply_bytes = h->factor_bytes = h->block_bytes = 0;
   h->launches = 0;
   h->colours_total = 0;
   h->coarse_total = 0;
+  resolve_pending(h);
   h->phases.clear();
   HS_CUDA(cudaMemsetAsync(h->d_err.p, 0, sizeof(DevError), h->st));
   cudaEvent_t e0, e1;
@@ -865,8 +923,9 @@ void factor_impl(hsolve_handle* h, double eps) {
   arena.alloc(cur->P.arena_elems * sizeof(real));
   HS_CUDA(cudaMemsetAsync(arena.p, 0, cur->P.arena_elems * sizeof(real), h->st));
   timed(h, "upload", 1, [&] {
-    Launch<real>::scatter_csr(h->d_csr_dst.as<int64_t>(), h->d_val.as<double>(), h->nnz,
-                              arena.as<real>(), h->st);
+    Launch<real>::scatter_csr(h->d_csr_dst.as<int64_t>(),
+                              h->opts.equilibrate ? h->d_fval.as<double>() : h->d_val.as<double>(),
+                              h->nnz, arena.as<real>(), h->st);
   });
   int level = 0;
   while (true) {
@@ -976,7 +1035,7 @@ void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int6
   if (realloc) h->drop_graphs();
   FLevel& F0 = *h->F[0];
   const int64_t n0 = F0.P.voff[F0.P.nclu];
-  Launch<real>::perm_in(h->d_perm.as<int64_t>(), h->n, rhs, ld, F0.vec.as<real>(), n0, nrhs, h->st);
+  Launch<real>::perm_in(h->d_perm.as<int64_t>(), hscale(h), h->n, rhs, ld, F0.vec.as<real>(), n0, nrhs, h->st);
   if (!h->use_graphs) {
     apply_levels<real>(h, nrhs, h->st);
   } else {
@@ -1007,7 +1066,7 @@ void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int6
     HS_CUDA(cudaGraphLaunch(g->exec, h->st));
     count_launch(g->nodes);
   }
-  Launch<real>::perm_out(h->d_perm.as<int64_t>(), h->n, F0.vec.as<real>(), n0, out, ld, nrhs, h->st);
+  Launch<real>::perm_out(h->d_perm.as<int64_t>(), hscale(h), h->n, F0.vec.as<real>(), n0, out, ld, nrhs, h->st);
 }
 
 void apply_any(hsolve_handle* h, const double* rhs, double* out, int nrhs, int64_t ld) {
@@ -1102,7 +1161,7 @@ void apply_scratch_impl(hsolve_handle* h, const double* rhs, double* out, int nr
   auto pt = [&](int l) { return reinterpret_cast<real*>(base + offs[3 * l + 2]); };
   FLevel& F0 = *h->F[0];
   const int64_t n0 = F0.P.voff[F0.P.nclu];
-  Launch<real>::perm_in(h->d_perm.as<int64_t>(), h->n, rhs, ld, vec(0), n0, nrhs, h->st);
+  Launch<real>::perm_in(h->d_perm.as<int64_t>(), hscale(h), h->n, rhs, ld, vec(0), n0, nrhs, h->st);
   for (int l = 0; l < L; l++) {
     FLevel& F = *h->F[l];
     const int64_t nl = std::max<int64_t>(F.P.voff[F.P.nclu], 1);
@@ -1133,7 +1192,7 @@ void apply_scratch_impl(hsolve_handle* h, const double* rhs, double* out, int nr
                               F.fac.as<real>(), F.vmap.as<int64_t>(), vec(l), zv(l), pt(l), nl,
                               nrhs, h->st);
   }
-  Launch<real>::perm_out(h->d_perm.as<int64_t>(), h->n, vec(0), n0, out, ld, nrhs, h->st);
+  Launch<real>::perm_out(h->d_perm.as<int64_t>(), hscale(h), h->n, vec(0), n0, out, ld, nrhs, h->st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1383,6 +1442,7 @@ void hsolve_default_opts(hsolve_opts* o) {
   o->gmres_restart = 50;
   o->compress = 0;
   o->cluster_qr = 1;
+  o->equilibrate = 0;
 }
 
 hsolve_status hsolve_analyze(const hsolve_csr* A, const double* coords, int dim,
@@ -1487,6 +1547,27 @@ hsolve_status hsolve_analyze(const hsolve_csr* A, const double* coords, int dim,
                             cudaMemcpyHostToDevice, h->st));
     HS_CUDA(cudaMemcpyAsync(h->d_perm.p, h->perm.data(), sizeof(int64_t) * n,
                             cudaMemcpyHostToDevice, h->st));
+    if (h->opts.equilibrate) {
+      // S = diag(|a_ii|)^{-1/2} (duplicates summed; 1 for a zero diagonal)
+      std::vector<double> dg(n, 0.0);
+      for (int64_t i = 0; i < n; i++)
+        for (int64_t p = h->rowptr[i]; p < h->rowptr[i + 1]; p++)
+          if (h->col[p] == i) dg[i] += h->val[p];
+      h->scale.resize(n);
+      for (int64_t i = 0; i < n; i++)
+        h->scale[i] = dg[i] != 0.0 ? 1.0 / std::sqrt(std::fabs(dg[i])) : 1.0;
+      std::vector<double> fv(h->nnz);
+      for (int64_t i = 0; i < n; i++)
+        for (int64_t p = h->rowptr[i]; p < h->rowptr[i + 1]; p++)
+          fv[p] = h->val[p] * h->scale[i] * h->scale[h->col[p]];
+      h->d_fval.alloc(sizeof(double) * std::max<int64_t>(h->nnz, 1));
+      h->d_scale.alloc(sizeof(double) * n);
+      HS_CUDA(cudaMemcpyAsync(h->d_fval.p, fv.data(), sizeof(double) * h->nnz,
+                              cudaMemcpyHostToDevice, h->st));
+      HS_CUDA(cudaMemcpyAsync(h->d_scale.p, h->scale.data(), sizeof(double) * n,
+                              cudaMemcpyHostToDevice, h->st));
+      HS_CUDA(cudaStreamSynchronize(h->st));
+    }
     HS_CUDA(cudaMemsetAsync(h->d_err.p, 0, sizeof(DevError), h->st));
     HS_CUDA(cudaStreamSynchronize(h->st));
   } catch (const Fail& f) {
@@ -1684,6 +1765,7 @@ hsolve_status hsolve_get_stats(const hsolve_handle* h, hsolve_stats* o) {
   o->kernel_launches = h->launches;
   o->precision = h->prec;
   o->launches_total = launches_total();
+  o->qr_flops = h->qr_flops;
   return HSOLVE_OK;
 }
 
@@ -1710,6 +1792,7 @@ hsolve_status hsolve_get_perm(const hsolve_handle* h, int64_t* perm) {
 hsolve_status hsolve_get_phase_times(const hsolve_handle* h, hsolve_phase_time* out, int32_t cap,
                                      int32_t* count) {
   if (!h || !count) return HSOLVE_ERR_ARG;
+  resolve_pending(const_cast<hsolve_handle*>(h));
   *count = (int)h->phases.size();
   for (int i = 0; i < (int)h->phases.size() && i < cap && out; i++) {
     std::memset(&out[i], 0, sizeof(out[i]));
@@ -1723,7 +1806,8 @@ hsolve_status hsolve_get_phase_times(const hsolve_handle* h, hsolve_phase_time* 
 hsolve_status hsolve_set_profiling(hsolve_handle* h, int on) {
   if (!h) return HSOLVE_ERR_ARG;
   h->profiling = on != 0;
-  h->profile_levels = on > 1;
+  h->profile_levels = on == 2;
+  h->profile_deferred = on == 3;
   return HSOLVE_OK;
 }
 

@@ -309,12 +309,12 @@ __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, 
   };
   if (pivot) {
     for (int q = threadIdx.x; q < c; q += blockDim.x) {
-      double s = 0;
+      real s = 0;
       for (int i = 0; i < m; i++) {
-        double v = at(i, q);
+        const real v = at(i, q);
         s += v * v;
       }
-      nrm2[q] = s;
+      nrm2[q] = (double)s;
       orig[q] = q;
     }
     __syncthreads();
@@ -410,7 +410,9 @@ __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, 
           for (int g = 0; g < CB; g++) w[g] += vi * x[rr][g];
         }
       }
-      double sq[CB];
+      // squared norms in the working precision: a float64 FMA per element
+      // here would bound the float32 path by the float64 rate
+      real sq[CB];
 #pragma unroll
       for (int g = 0; g < CB; g++) {
         w[g] *= rt;
@@ -432,14 +434,14 @@ __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, 
             if (!ok[g]) continue;
             const real v = x[rr][g] - w[g] * vi;
             at(i + rr, t0 + g * nth) = v;
-            if (i + rr > j) sq[g] += (double)v * (double)v;
+            if (i + rr > j) sq[g] += v * v;
           }
         }
       }
       if (pivot)
 #pragma unroll
         for (int g = 0; g < CB; g++)
-          if (ok[g]) nrm2[t0 + g * nth] = sq[g];
+          if (ok[g]) nrm2[t0 + g * nth] = (double)sq[g];
     }
     __syncthreads();
     k = j + 1;

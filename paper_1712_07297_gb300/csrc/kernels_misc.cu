@@ -341,26 +341,30 @@ __global__ void scatter_vec_kernel(const int64_t* __restrict__ idx, int64_t n,
 }
 
 template <typename real>
-__global__ void perm_in_kernel(const int64_t* __restrict__ perm, int64_t n,
-                               const double* __restrict__ src, int64_t lds, real* __restrict__ dst,
-                               int64_t ldd, int nrhs) {
+__global__ void perm_in_kernel(const int64_t* __restrict__ perm, const double* __restrict__ S,
+                               int64_t n, const double* __restrict__ src, int64_t lds,
+                               real* __restrict__ dst, int64_t ldd, int nrhs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs;
        e += (int64_t)gridDim.x * blockDim.x) {
     int64_t p = e % n;
     int r = (int)(e / n);
-    dst[p + r * ldd] = (real)src[perm[p] + r * lds];
+    const int64_t g = perm[p];
+    const double v = src[g + r * lds];
+    dst[p + r * ldd] = (real)(S ? S[g] * v : v);
   }
 }
 
 template <typename real>
-__global__ void perm_out_kernel(const int64_t* __restrict__ perm, int64_t n,
-                                const real* __restrict__ src, int64_t lds, double* __restrict__ dst,
-                                int64_t ldd, int nrhs) {
+__global__ void perm_out_kernel(const int64_t* __restrict__ perm, const double* __restrict__ S,
+                                int64_t n, const real* __restrict__ src, int64_t lds,
+                                double* __restrict__ dst, int64_t ldd, int nrhs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs;
        e += (int64_t)gridDim.x * blockDim.x) {
     int64_t p = e % n;
     int r = (int)(e / n);
-    dst[perm[p] + r * ldd] = (double)src[p + r * lds];
+    const int64_t g = perm[p];
+    const double v = (double)src[p + r * lds];
+    dst[g + r * ldd] = S ? S[g] * v : v;
   }
 }
 
@@ -533,19 +537,21 @@ void Launch<real>::scatter_vec(const int64_t* idx, int64_t n, const real* src, i
 }
 
 template <typename real>
-void Launch<real>::perm_in(const int64_t* perm, int64_t n, const double* src, int64_t lds,
-                           real* dst, int64_t ldd, int nrhs, cudaStream_t st) {
+void Launch<real>::perm_in(const int64_t* perm, const double* S, int64_t n, const double* src,
+                           int64_t lds, real* dst, int64_t ldd, int nrhs, cudaStream_t st) {
   if (n <= 0) return;
   count_launch();
-  perm_in_kernel<real><<<grid_for(n * nrhs, 256), 256, 0, st>>>(perm, n, src, lds, dst, ldd, nrhs);
+  perm_in_kernel<real><<<grid_for(n * nrhs, 256), 256, 0, st>>>(perm, S, n, src, lds, dst, ldd,
+                                                                  nrhs);
 }
 
 template <typename real>
-void Launch<real>::perm_out(const int64_t* perm, int64_t n, const real* src, int64_t lds,
-                            double* dst, int64_t ldd, int nrhs, cudaStream_t st) {
+void Launch<real>::perm_out(const int64_t* perm, const double* S, int64_t n, const real* src,
+                            int64_t lds, double* dst, int64_t ldd, int nrhs, cudaStream_t st) {
   if (n <= 0) return;
   count_launch();
-  perm_out_kernel<real><<<grid_for(n * nrhs, 256), 256, 0, st>>>(perm, n, src, lds, dst, ldd, nrhs);
+  perm_out_kernel<real><<<grid_for(n * nrhs, 256), 256, 0, st>>>(perm, S, n, src, lds, dst, ldd,
+                                                                   nrhs);
 }
 
 

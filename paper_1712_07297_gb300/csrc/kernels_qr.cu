@@ -172,13 +172,15 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
     for (int i = lane; i < m; i += 32) Gs[i + (int64_t)d * ldsm] = arena[p + (int64_t)i * st];
   }
   __syncthreads();
+  // squared norms in the working precision (float64 arithmetic per element
+  // would bound the float32 path by the float64 rate); compared in float64
   for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
-    double s = 0;
+    real s = 0;
     for (int i = 0; i < m; i++) {
-      double x = Gs[i + (int64_t)t * ldsm];
+      const real x = Gs[i + (int64_t)t * ldsm];
       s += x * x;
     }
-    nrm[t] = s;
+    nrm[t] = (double)s;
   }
   __syncthreads();
 
@@ -276,13 +278,13 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
       real w = 0;
       for (int i = j; i < m; i++) w += vloc[i] * col[i];
       w *= tj;
-      double s = 0;
+      real s = 0;
       for (int i = j; i < m; i++) {
         const real v = col[i] - w * vloc[i];
         col[i] = v;
-        if (i > j) s += (double)v * (double)v;
+        if (i > j) s += v * v;
       }
-      nrm[t] = s;
+      nrm[t] = (double)s;
     }
     __syncthreads();
     k = j + 1;

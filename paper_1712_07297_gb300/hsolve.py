@@ -38,7 +38,7 @@ class Csr(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("symmetric", C.c_int32), ("top_size", C.c_int64),
                 ("max_rank", C.c_int32), ("gmres_restart", C.c_int32), ("compress", C.c_int32),
-                ("cluster_qr", C.c_int32)]
+                ("cluster_qr", C.c_int32), ("equilibrate", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -53,7 +53,8 @@ class Stats(C.Structure):
                 ("apply_bytes", C.c_int64), ("factor_flops", C.c_double),
                 ("schur_flops", C.c_double), ("prep_flops", C.c_double),
                 ("gemm_flops", C.c_double), ("kernel_launches", C.c_int32),
-                ("precision", C.c_int32), ("launches_total", C.c_int64)]
+                ("precision", C.c_int32), ("launches_total", C.c_int64),
+                ("qr_flops", C.c_double)]
 
 
 class PhaseTime(C.Structure):
@@ -134,7 +135,8 @@ class Solver:
     """One analysed matrix: analyze -> factor -> apply / solve."""
 
     def __init__(self, rowptr, col, val, coords=None, *, leaf_size=128, symmetric=-1, top_size=0,
-                 max_rank=0, gmres_restart=50, compress=0, cluster_qr=1, stream=None):
+                 max_rank=0, gmres_restart=50, compress=0, cluster_qr=1, equilibrate=0,
+                 stream=None):
         lib = load()
         self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         self.col = np.ascontiguousarray(col, dtype=np.int32)
@@ -146,6 +148,7 @@ class Solver:
         o.leaf_size, o.symmetric, o.top_size = leaf_size, symmetric, top_size
         o.max_rank, o.gmres_restart, o.compress = max_rank, gmres_restart, compress
         o.cluster_qr = cluster_qr
+        o.equilibrate = equilibrate
         h = C.c_void_p()
         cptr, dim = None, 0
         if coords is not None:
@@ -254,8 +257,8 @@ class Solver:
         _check(load().hsolve_get_perm(self.h, p.ctypes.data), self.h)
         return p
 
-    def set_profiling(self, on, per_level=False):
-        v = 0 if not on else (2 if per_level else 1)
+    def set_profiling(self, on, per_level=False, deferred=False):
+        v = 0 if not on else (2 if per_level else (3 if deferred else 1))
         _check(load().hsolve_set_profiling(self.h, v), self.h)
 
     def phase_times(self) -> dict:

@@ -218,7 +218,7 @@ def workload(name: str):
         "poisson3d_64": (lambda: poisson((64, 64, 64)), dict(leaf=128, eps=1e-2, nrhs=1, krylov="pcg", rhs_seed=1001)),
         "poisson3d_32": (lambda: poisson((32, 32, 32)), dict(leaf=128, eps=1e-2, nrhs=1, krylov="pcg", rhs_seed=1001)),
         "poisson3d_16": (lambda: poisson((16, 16, 16)), dict(leaf=64, eps=1e-2, nrhs=1, krylov="pcg", rhs_seed=1001)),
-        "vcdiff3d_96": (lambda: vc_diffusion((96, 96, 96), seed=2002), dict(leaf=128, eps=1e-2, nrhs=1, krylov="pcg", rhs_seed=1002)),
+        "vcdiff3d_96": (lambda: vc_diffusion((96, 96, 96), seed=2002), dict(leaf=128, eps=1e-2, nrhs=1, krylov="pcg", rhs_seed=1002, equilibrate=1)),
         "convdiff3d_64": (lambda: convection_diffusion((64, 64, 64), 10.0), dict(leaf=128, eps=1e-2, nrhs=1, krylov="gmres", rhs_seed=1002)),
         "poisson3d_128": (lambda: poisson((128, 128, 128)), dict(leaf=128, eps=1e-2, nrhs=8, krylov="gmres", rhs_seed=1003)),
     }[name]

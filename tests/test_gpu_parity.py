@@ -293,3 +293,41 @@ def test_dense_top_blocked(hs, precision):
     for c in range(2):
         assert np.linalg.norm(b[c] - p.scipy() @ xx[c]) <= 1.0001e-10 * np.linalg.norm(b[c])
     s.close()
+
+
+def _equilibrated(p):
+    """S A S with S = diag(|a_ii|)^{-1/2}, and S (the definition the library's
+    equilibrate option states)."""
+    import dataclasses
+    rows = np.repeat(np.arange(p.n), np.diff(p.rowptr))
+    d = np.zeros(p.n)
+    np.add.at(d, rows[rows == p.col], p.val[rows == p.col])
+    S = np.where(d != 0, 1.0 / np.sqrt(np.abs(np.where(d != 0, d, 1.0))), 1.0)
+    return dataclasses.replace(p, val=p.val * S[rows] * S[p.col]), S
+
+
+@pytest.mark.parametrize("mk,leaf,eps,sym", [
+    (lambda: I.vc_diffusion((16, 16, 16), seed=2002), 64, 1e-2, 1),
+    (lambda: I.high_contrast((14, 13, 12), seed=5), 40, 1e-3, 1),
+    (lambda: I.convection_diffusion((30, 26), 10.0), 32, 1e-2, 0),
+])
+def test_equilibrate_matches_oracle(hs, mk, leaf, eps, sym):
+    # M^{-1} = S Mh^{-1} S with Mh the oracle's factorization of S A S; ranks
+    # are those of S A S
+    p = mk()
+    q, S = _equilibrated(p)
+    fac = H.factor(q.rowptr, q.col, q.val, q.coords, leaf, eps, symmetric=bool(sym))
+    s = hs.Solver.from_problem(p, leaf_size=leaf, symmetric=sym, equilibrate=1)
+    s.factor(eps, "fp64")
+    if sym:
+        assert _ranks_match(s, fac) >= 1
+    b = I.rhs(p.n, 2, seed=1004)
+    ref = S[None, :] * H.solve(fac, (S[None, :] * b).T).T
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out, ref) < 1e-10, _rel(out, ref)
+    x, info = s.solve(torch.from_numpy(b).cuda(), krylov="pcg" if sym else "gmres", tol=1e-10)
+    A = p.scipy()
+    x = x.cpu().numpy()
+    for c in range(2):
+        assert np.linalg.norm(b[c] - A @ x[c]) <= 1e-10 * np.linalg.norm(b[c]) * 1.0001
+    s.close()
