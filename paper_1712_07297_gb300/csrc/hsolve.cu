@@ -228,6 +228,7 @@ struct hsolve_handle {
 };
 
 namespace {
+constexpr int kNumSMs = 152;  // SMs of one GB300 (2 dies x 76)
 // the equilibration S by original index, or null when A is factored itself
 const double* hscale(const hsolve_handle* h) {
   return h->opts.equilibrate ? h->d_scale.as<double>() : nullptr;
@@ -669,7 +670,12 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       HS_CUDA(cudaStreamSynchronize(h->st));
       for (size_t i = 0; i < qrt.size(); i++) nzcols[qrt[i].s] = cnt[i];
       const int nzmax = std::max(1, *std::max_element(cnt.begin(), cnt.end()));
-      const int CL = Launch<real>::qr_cluster_size(qm, nzmax);
+      int CL = Launch<real>::qr_cluster_size(qm, nzmax);
+      // a class of few clusters spreads each block over more CTAs (up to the
+      // portable cluster size 8, at least 64 columns each) to occupy the SMs
+      if (CL > 0)
+        while (CL < 8 && (int64_t)qrt.size() * CL * 2 <= 2 * kNumSMs && nzmax >= CL * 2 * 64)
+          CL *= 2;
       if (CL > 0) {
         for (auto& pt : prep)
           if (pt.l == 0 && pt.ncolG > 0) pt.qr = 2;

@@ -109,94 +109,101 @@ __device__ void cta_gemm(int M, int N, int K, const real* A, int lda, bool ta, c
   __syncthreads();
 }
 
+// The helpers below map warps to columns and lanes to rows: column-major
+// accesses are then contiguous across a warp, and no per-element index
+// division is needed.
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+__device__ __forceinline__ int num_warps() { return blockDim.x >> 5; }
+
+template <typename real>
+__device__ __forceinline__ real warp_sum(real v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <typename real>
 __device__ void cta_copy(int M, int N, const real* A, int64_t lda, real* B, int64_t ldb) {
-  for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
-    int i = idx % M, j = idx / M;
-    B[i + j * ldb] = A[i + j * lda];
-  }
+  for (int j = warp_id(); j < N; j += num_warps())
+    for (int i = lane_id(); i < M; i += 32) B[i + j * ldb] = A[i + j * lda];
   __syncthreads();
 }
 
 // Zero the strict upper (upper=true) or strict lower part of an n x n matrix.
 template <typename real>
 __device__ void cta_zero_tri(int n, real* A, int lda, bool upper) {
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    int i = idx % n, j = idx / n;
-    if (upper ? (i < j) : (i > j)) A[i + (int64_t)j * lda] = 0;
+  for (int j = warp_id(); j < n; j += num_warps()) {
+    const int i0 = upper ? 0 : j + 1, i1 = upper ? j : n;
+    for (int i = i0 + lane_id(); i < i1; i += 32) A[i + (int64_t)j * lda] = 0;
   }
   __syncthreads();
 }
 
 template <typename real>
 __device__ void cta_identity(int M, int N, int diag_off, real* A, int lda) {
-  for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
-    int i = idx % M, j = idx / M;
-    A[i + (int64_t)j * lda] = (i == j + diag_off) ? real(1) : real(0);
-  }
+  for (int j = warp_id(); j < N; j += num_warps())
+    for (int i = lane_id(); i < M; i += 32)
+      A[i + (int64_t)j * lda] = (i == j + diag_off) ? real(1) : real(0);
   __syncthreads();
 }
 
-// In-place lower Cholesky A = L L^T (lower triangle).  Returns false on every
+// In-place lower Cholesky A = L L^T (lower triangle), right-looking, one
+// barrier per step: step j subtracts a_ij a_lj / a_jj from the trailing lower
+// triangle and, in the same phase, finishes column j-1 (scaling by
+// 1/sqrt(d_{j-1})), which step j does not read.  Returns false on every
 // thread for a non-positive pivot.
 template <typename real>
 __device__ bool cta_cholesky(int n, real* A, int lda, int* sflag) {
+  (void)sflag;
+  const int lane = lane_id(), warp = warp_id(), nw = num_warps();
+  real rprev = 0;  // 1 / sqrt(d_{j-1})
   for (int j = 0; j < n; j++) {
-    if (threadIdx.x == 0) {
-      real d = A[j + (int64_t)j * lda];
-      if (!(d > real(0))) *sflag = 1;
-      else A[j + (int64_t)j * lda] = sqrt_(d);
+    const real d = A[j + (int64_t)j * lda];
+    if (!(d > real(0))) return false;  // uniform: every thread read the same d
+    const real invd = real(1) / d;
+    if (j > 0) {
+      real* cp = A + (int64_t)(j - 1) * lda;
+      for (int i = j + threadIdx.x; i < n; i += blockDim.x) cp[i] *= rprev;
+    }
+    const real* cj = A + (int64_t)j * lda;
+    for (int l = j + 1 + warp; l < n; l += nw) {
+      const real alj = cj[l] * invd;
+      real* cl = A + (int64_t)l * lda;
+      for (int i = l + lane; i < n; i += 32) cl[i] -= cj[i] * alj;
     }
     __syncthreads();
-    if (*sflag) return false;
-    const real rd = real(1) / A[j + (int64_t)j * lda];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (int64_t)j * lda] *= rd;
-    __syncthreads();
-    const int t = n - j - 1;
-    for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
-      int i = j + 1 + idx % t, l = j + 1 + idx / t;
-      if (i >= l) A[i + (int64_t)l * lda] -= A[i + (int64_t)j * lda] * A[l + (int64_t)j * lda];
-    }
-    __syncthreads();
+    // the diagonal of column j-1 was read as d in the previous step only
+    if (j > 0 && threadIdx.x == 0) A[(j - 1) + (int64_t)(j - 1) * lda] = real(1) / rprev;
+    rprev = real(1) / sqrt_(d);
   }
+  if (n > 0 && threadIdx.x == 0) A[(n - 1) + (int64_t)(n - 1) * lda] = real(1) / rprev;
+  __syncthreads();
   return true;
 }
 
 // In-place LU with partial pivoting, P A = L U (unit lower L).  piv[j] = row
 // swapped with j at step j.  Near-ties (|a| >= (1 - 1e-10) max) go to the
 // lowest row.  Returns false for an exactly zero pivot column.
+__device__ double cta_max_d(double v, double* red);
+__device__ int cta_min_i(int v, int* red);
+
 template <typename real>
 __device__ bool cta_lu(int n, real* A, int lda, int* piv, double* red_d, int* red_i,
                        int* sflag) {
+  (void)sflag;
+  const int lane = lane_id(), warp = warp_id(), nw = num_warps();
   for (int j = 0; j < n; j++) {
     double mx = 0;
     for (int i = j + threadIdx.x; i < n; i += blockDim.x)
       mx = fmax(mx, fabs((double)A[i + (int64_t)j * lda]));
-    red_d[threadIdx.x] = mx;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) red_d[threadIdx.x] = fmax(red_d[threadIdx.x], red_d[threadIdx.x + s]);
-      __syncthreads();
-    }
-    mx = red_d[0];
-    __syncthreads();
+    mx = cta_max_d(mx, red_d);
+    if (!(mx > 0.0)) return false;  // uniform
     int best = n;
     for (int i = j + threadIdx.x; i < n; i += blockDim.x)
       if (fabs((double)A[i + (int64_t)j * lda]) >= (1.0 - kPivotTieRtol) * mx && i < best) best = i;
-    red_i[threadIdx.x] = best;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) red_i[threadIdx.x] = min(red_i[threadIdx.x], red_i[threadIdx.x + s]);
-      __syncthreads();
-    }
-    const int p = red_i[0];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      piv[j] = p;
-      if (!(mx > 0.0)) *sflag = 1;
-    }
-    __syncthreads();
-    if (*sflag) return false;
+    const int p = cta_min_i(best, red_i);
+    if (threadIdx.x == 0) piv[j] = p;
     if (p != j)
       for (int c = threadIdx.x; c < n; c += blockDim.x) {
         real t = A[j + (int64_t)c * lda];
@@ -204,36 +211,47 @@ __device__ bool cta_lu(int n, real* A, int lda, int* piv, double* red_d, int* re
         A[p + (int64_t)c * lda] = t;
       }
     __syncthreads();
+    // l_ij = a_ij / a_jj is formed on the fly by every column's update and
+    // written back in the next phase
     const real rd = real(1) / A[j + (int64_t)j * lda];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (int64_t)j * lda] *= rd;
-    __syncthreads();
-    const int t = n - j - 1;
-    for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
-      int i = j + 1 + idx % t, l = j + 1 + idx / t;
-      A[i + (int64_t)l * lda] -= A[i + (int64_t)j * lda] * A[j + (int64_t)l * lda];
+    const real* cj = A + (int64_t)j * lda;
+    for (int l = j + 1 + warp; l < n; l += nw) {
+      real* cl = A + (int64_t)l * lda;
+      const real ujl = cl[j];
+      for (int i = j + 1 + lane; i < n; i += 32) cl[i] -= (cj[i] * rd) * ujl;
     }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (int64_t)j * lda] *= rd;
     __syncthreads();
   }
   return true;
 }
 
-// In-place inverse of a lower triangular matrix (unit diagonal if `unit`,
-// diagonal then left untouched), column by column from the last: the
-// trailing part is already inverted when column j is formed.  tmp: n reals.
+// X = L^{-1} for lower triangular L (unit diagonal if `unit`), out of place:
+// X (n x n, zero above the diagonal) starts as I and every step i subtracts
+// l_ri x_ic for rows r > i from all columns c <= i (x_ic = x_ic / l_ii on the
+// fly); row i is finished in the next phase.  One barrier per step.
 template <typename real>
-__device__ void cta_trtri_lower(int n, real* L, int ld, bool unit, real* tmp) {
-  for (int j = n - 1; j >= 0; j--) {
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) tmp[i] = L[i + (int64_t)j * ld];
-    if (threadIdx.x == 0 && !unit) L[j + (int64_t)j * ld] = real(1) / L[j + (int64_t)j * ld];
-    __syncthreads();
-    const real d = unit ? real(1) : L[j + (int64_t)j * ld];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      real acc = 0;
-      for (int l = j + 1; l <= i; l++) acc += (l == i && unit ? real(1) : L[i + (int64_t)l * ld]) * tmp[l];
-      L[i + (int64_t)j * ld] = -acc * d;
+__device__ void cta_trtri_lower_oop(int n, const real* L, int ldl, bool unit, real* X, int ldx) {
+  const int lane = lane_id(), warp = warp_id(), nw = num_warps();
+  cta_identity<real>(n, n, 0, X, ldx);
+  real dprev = 1;
+  for (int i = 0; i < n; i++) {
+    const real di = unit ? real(1) : real(1) / L[i + (int64_t)i * ldl];
+    if (i > 0 && !unit)
+      for (int c = threadIdx.x; c < i; c += blockDim.x) X[(i - 1) + (int64_t)c * ldx] *= dprev;
+    const real* li = L + (int64_t)i * ldl;
+    for (int c = warp; c <= i; c += nw) {
+      real* xc = X + (int64_t)c * ldx;
+      const real xic = xc[i] * di;
+      for (int r = i + 1 + lane; r < n; r += 32) xc[r] -= li[r] * xic;
     }
+    dprev = di;
     __syncthreads();
   }
+  if (n > 0 && !unit)
+    for (int c = threadIdx.x; c < n; c += blockDim.x) X[(n - 1) + (int64_t)c * ldx] *= dprev;
+  __syncthreads();
 }
 
 // In-place inverse of an upper triangular matrix, column by column from the
@@ -254,38 +272,36 @@ __device__ void cta_trtri_upper(int n, real* U, int ld, real* tmp) {
   }
 }
 
+// Block reductions: shuffle within each warp, one exchange through shared
+// memory (red: at least one slot per warp), two barriers.
 __device__ double cta_max_d(double v, double* red) {
-  red[threadIdx.x] = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane_id() == 0) red[warp_id()] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
-  }
   double r = red[0];
+  for (int w = 1; w < num_warps(); w++) r = fmax(r, red[w]);
   __syncthreads();
   return r;
 }
 
 __device__ int cta_min_i(int v, int* red) {
-  red[threadIdx.x] = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane_id() == 0) red[warp_id()] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = min(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
-  }
   int r = red[0];
+  for (int w = 1; w < num_warps(); w++) r = min(r, red[w]);
   __syncthreads();
   return r;
 }
 
 __device__ double cta_sum_d(double v, double* red) {
-  red[threadIdx.x] = v;
+  v = warp_sum(v);
+  if (lane_id() == 0) red[warp_id()] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  double r = red[0];
+  double r = 0;
+  for (int w = 0; w < num_warps(); w++) r += red[w];
   __syncthreads();
   return r;
 }
@@ -450,37 +466,136 @@ __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, 
   return k;
 }
 
-// Q[:, c0:c0+ncols] of Q = H_0 .. H_{k-1}: out (m x ncols) starts as the
-// identity columns c0.. and receives the reflectors in reverse order.
+// Q[:, c0:c0+ncols] of Q = H_0 .. H_{k-1} (H_j = I - tau_j v_j v_j^T, v_j in
+// rows j..m of column j of V): out (m x ncols) starts as the identity columns
+// c0.. and receives the reflectors in reverse order.  One warp per group of
+// four columns; lane l owns rows l, l + 32, ... of them (held in registers
+// when m <= 256), so the warps never wait for one another and the lanes only
+// exchange the four dot products of each reflector (shuffles).
 template <typename real, bool RowMajor>
 __device__ void cta_form_q(int m, int k, const real* V, int ldv, const real* tau, int c0,
                            int ncols, real* out, int ldo, real* vsh) {
-  cta_identity<real>(m, ncols, c0, out, ldo);
-  constexpr int RB = 8;
-  for (int j = k - 1; j >= 0; j--) {
-    for (int i = j + threadIdx.x; i < m; i += blockDim.x)
-      vsh[i] = RowMajor ? V[(int64_t)i * ldv + j] : V[i + (int64_t)j * ldv];
-    __syncthreads();
-    const real tj = tau[j];
-    for (int t = threadIdx.x; t < ncols; t += blockDim.x) {
-      real* col = out + (int64_t)t * ldo;
-      real w = 0;
-      for (int i = j; i < m; i += RB) {
-        real x[RB];
+  (void)vsh;
+  constexpr int CW = 4, R = 8;
+  const int lane = lane_id(), warp = warp_id(), nw = num_warps();
+  auto vat = [&](int i, int j) -> real {
+    return RowMajor ? V[(int64_t)i * ldv + j] : V[i + (int64_t)j * ldv];
+  };
+  for (int g0 = warp * CW; g0 < ncols; g0 += nw * CW) {
+    const int ng = min(CW, ncols - g0);
+    if (m <= 32 * R) {
+      real x[R][CW];
 #pragma unroll
-        for (int rr = 0; rr < RB; rr++) x[rr] = (i + rr < m) ? col[i + rr] : real(0);
+      for (int r = 0; r < R; r++)
 #pragma unroll
-        for (int rr = 0; rr < RB; rr++)
-          if (i + rr < m) w += vsh[i + rr] * x[rr];
+        for (int g = 0; g < CW; g++) x[r][g] = (lane + 32 * r == c0 + g0 + g) ? real(1) : real(0);
+      for (int j = k - 1; j >= 0; j--) {
+        const real tj = tau[j];
+        real v[R], d[CW];
+#pragma unroll
+        for (int g = 0; g < CW; g++) d[g] = 0;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          const int i = lane + 32 * r;
+          v[r] = (i >= j && i < m) ? vat(i, j) : real(0);
+#pragma unroll
+          for (int g = 0; g < CW; g++) d[g] += v[r] * x[r][g];
+        }
+#pragma unroll
+        for (int g = 0; g < CW; g++) d[g] = warp_sum(d[g]) * tj;
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+          for (int g = 0; g < CW; g++) x[r][g] -= d[g] * v[r];
       }
-      w *= tj;
-      for (int i = j; i < m; i += RB) {
-        real x[RB];
 #pragma unroll
-        for (int rr = 0; rr < RB; rr++) x[rr] = (i + rr < m) ? col[i + rr] : real(0);
+      for (int r = 0; r < R; r++) {
+        const int i = lane + 32 * r;
+        if (i < m)
 #pragma unroll
-        for (int rr = 0; rr < RB; rr++)
-          if (i + rr < m) col[i + rr] = x[rr] - w * vsh[i + rr];
+          for (int g = 0; g < CW; g++)
+            if (g < ng) out[i + (int64_t)(g0 + g) * ldo] = x[r][g];
+      }
+    } else {
+      for (int g = 0; g < ng; g++)
+        for (int i = lane; i < m; i += 32)
+          out[i + (int64_t)(g0 + g) * ldo] = (i == c0 + g0 + g) ? real(1) : real(0);
+      for (int j = k - 1; j >= 0; j--) {
+        const real tj = tau[j];
+        real d[CW];
+#pragma unroll
+        for (int g = 0; g < CW; g++) d[g] = 0;
+        for (int i = lane; i < m; i += 32) {
+          if (i < j) continue;
+          const real v = vat(i, j);
+#pragma unroll
+          for (int g = 0; g < CW; g++)
+            if (g < ng) d[g] += v * out[i + (int64_t)(g0 + g) * ldo];
+        }
+#pragma unroll
+        for (int g = 0; g < CW; g++) d[g] = warp_sum(d[g]) * tj;
+        for (int i = lane; i < m; i += 32) {
+          if (i < j) continue;
+          const real v = vat(i, j);
+#pragma unroll
+          for (int g = 0; g < CW; g++)
+            if (g < ng) out[i + (int64_t)(g0 + g) * ldo] -= d[g] * v;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Householder QR without pivoting of the m x k matrix X (column-major, in
+// place): v_j in rows j..m of column j (its head x_jj - beta, beta =
+// -sign(x_jj) ||x_j||), tau[j] = 1 / (r (r + |x_jj|)).  Step j: the warp
+// owning column j forms the reflector; after a barrier every warp applies it
+// to its columns t > j, four at a time (lanes over rows, shuffled dots).
+template <typename real>
+__device__ void cta_qr_np(int m, int k, real* X, int ldx, real* tau) {
+  constexpr int CW = 4;
+  const int lane = lane_id(), warp = warp_id(), nw = num_warps();
+  for (int j = 0; j < k; j++) {
+    if (warp == j % nw) {
+      real* xj = X + (int64_t)j * ldx;
+      real sq = 0;
+      for (int i = j + lane; i < m; i += 32) sq += xj[i] * xj[i];
+      sq = warp_sum(sq);
+      const double r = sqrt((double)sq);
+      const double x0 = (double)xj[j];
+      const double beta = (x0 >= 0.0) ? -r : r;
+      const double tj = (r > 0.0) ? 1.0 / (r * (r + fabs(x0))) : 0.0;
+      __syncwarp();
+      if (lane == 0) {
+        xj[j] = (real)(x0 - beta);
+        tau[j] = (real)tj;
+      }
+    }
+    __syncthreads();
+    const real* vj = X + (int64_t)j * ldx;
+    const real tj = tau[j];
+    for (int t0 = j + 1 + warp; t0 < k; t0 += nw * CW) {
+      real d[CW];
+#pragma unroll
+      for (int g = 0; g < CW; g++) d[g] = 0;
+      for (int i = j + lane; i < m; i += 32) {
+        const real v = vj[i];
+#pragma unroll
+        for (int g = 0; g < CW; g++) {
+          const int t = t0 + g * nw;
+          if (t < k) d[g] += v * X[i + (int64_t)t * ldx];
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < CW; g++) d[g] = warp_sum(d[g]) * tj;
+      for (int i = j + lane; i < m; i += 32) {
+        const real v = vj[i];
+#pragma unroll
+        for (int g = 0; g < CW; g++) {
+          const int t = t0 + g * nw;
+          if (t < k) X[i + (int64_t)t * ldx] -= d[g] * v;
+        }
       }
     }
     __syncthreads();
@@ -545,8 +660,8 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
   // shared-memory matrices get an odd leading dimension: loops that give one
   // column to each thread then touch 32 different banks
   const int64_t reg = (int64_t)(smem_m | 1) * smem_m;  // one shared region
-  const int ldA = smem_mats >= 1 ? (m | 1) : m;
-  const int ldB = smem_mats >= 2 ? (m | 1) : m;
+  int ldA = smem_mats >= 1 ? (m | 1) : m;
+  int ldB = smem_mats >= 2 ? (m | 1) : m;
   const int ldU = smem_mats >= 3 ? (m | 1) : m;
   real* W_A = smem_mats >= 1 ? smat : ws;                  // A_ss -> factor -> inverse factor
   real* W_B = smem_mats >= 2 ? smat + reg : ws + mm;       // A_ss^{-1}
@@ -680,21 +795,24 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
   const int f = m - k;
 
   if (sym) {
-    // L^{-1} in place (lower), then B = L^{-T} L^{-1}
-    cta_trtri_lower<real>(m, W_A, ldA, false, tsh);
-    cta_zero_tri<real>(m, W_A, ldA, true);
+    // L^{-1} into the home of A_ss^{-1}, then B = L^{-T} L^{-1} into the
+    // home of the (spent) factor; the two buffers then trade names
+    cta_trtri_lower_oop<real>(m, W_A, ldA, false, W_B, ldB);
     if (k == 0) {  // E_s = I: T' = L^{-1}
-      cta_copy<real>(m, m, W_A, ldA, T, m);
+      cta_copy<real>(m, m, W_B, ldB, T, m);
       return;
     }
-    cta_gemm<real>(m, m, m, W_A, ldA, true, W_A, ldA, false, W_B, ldB, real(1), real(0), gsh);
+    cta_gemm<real>(m, m, m, W_B, ldB, true, W_B, ldB, false, W_A, ldA, real(1), real(0), gsh);
+    real* tp = W_A;
+    W_A = W_B;
+    W_B = tp;
+    const int tl = ldA;
+    ldA = ldB;
+    ldB = tl;
   } else {
     // L^{-1} (unit lower) into W_L, U^{-1} into W_S
-    cta_copy<real>(m, m, W_A, ldA, W_L, m);
+    cta_trtri_lower_oop<real>(m, W_A, ldA, true, W_L, m);
     cta_copy<real>(m, m, W_A, ldA, W_S, m);
-    cta_trtri_lower<real>(m, W_L, m, true, tsh);
-    cta_zero_tri<real>(m, W_L, m, true);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) W_L[i + (int64_t)i * m] = real(1);
     cta_trtri_upper<real>(m, W_S, m, tsh);
     cta_zero_tri<real>(m, W_S, m, false);
     if (k == 0) {
@@ -734,8 +852,7 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
     ldX = ldA;
   }
   cta_gemm<real>(m, k, m, W_B, ldB, false, W_U, ldU, false, W_X, ldX, real(1), real(0), gsh);
-  cta_householder_qr<real, false>(m, k, W_X, ldX, nrm2, orig, tau2, false, 0.0, k, 0.0, red_d,
-                                  red_i, vsh);
+  cta_qr_np<real>(m, k, W_X, ldX, tau2);
   W_V = W_U + (int64_t)k * ldU;
   cta_form_q<real, false>(m, k, W_X, ldX, tau2, k, f, W_V, ldU, vsh);
 
@@ -755,18 +872,16 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
       report<real>(err, (int)HSOLVE_ERR_NOT_SPD, tk.s, level, rank, m);
       return;
     }
-    cta_trtri_lower<real>(f, W_F, ldF, false, tsh);
-    cta_zero_tri<real>(f, W_F, ldF, true);
+    cta_trtri_lower_oop<real>(f, W_F, ldF, false, W_L, m);
     cta_copy<real>(k, m, W_T, m, T, m);
-    cta_gemm<real>(f, m, f, W_F, ldF, false, W_T + k, m, false, T + k, m, real(1), real(0), gsh);
+    cta_gemm<real>(f, m, f, W_L, m, false, W_T + k, m, false, T + k, m, real(1), real(0), gsh);
     // D = C U^T (k x m) for the coarse-to-far update C (U^T A_sw)
     cta_gemm<real>(k, m, k, W_C, m, false, W_U, ldU, true, ws_all + tk.D, m, real(1), real(0),
                    gsh);
   } else {
     // V_R: complement of B^T U
     cta_gemm<real>(m, k, m, W_B, ldB, true, W_U, ldU, false, W_X, m, real(1), real(0), gsh);
-    cta_householder_qr<real, false>(m, k, W_X, m, nrm2, orig, tau2, false, 0.0, k, 0.0, red_d,
-                                    red_i, vsh);
+    cta_qr_np<real>(m, k, W_X, m, tau2);
     cta_form_q<real, false>(m, k, W_X, m, tau2, k, f, W_R, m, vsh);
     // F = V_L^T B V_R (f x f) and its LU
     cta_gemm<real>(f, f, m, W_T + k, m, false, W_R, m, false, W_F, m, real(1), real(0), gsh);
@@ -785,11 +900,7 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
         }
       __syncthreads();
     }
-    cta_copy<real>(f, f, W_F, m, W_L, m);
-    cta_trtri_lower<real>(f, W_L, m, true, tsh);
-    cta_zero_tri<real>(f, W_L, m, true);
-    for (int i = threadIdx.x; i < f; i += blockDim.x) W_L[i + (int64_t)i * m] = real(1);
-    __syncthreads();
+    cta_trtri_lower_oop<real>(f, W_F, m, true, W_L, m);
     cta_copy<real>(k, m, W_T, m, T, m);
     cta_gemm<real>(f, m, f, W_L, m, false, W_T + k, m, false, T + k, m, real(1), real(0), gsh);
     // T'_R = B [U, V_R U_F^{-1}]; store its transpose
