@@ -207,6 +207,23 @@ hsolve_status hsolve_solve_host(hsolve_handle* h, hsolve_krylov krylov,
 hsolve_status hsolve_spmv(hsolve_handle* h, const double* x, double* y,
                           int nrhs, int64_t ld);
 
+/* The tensor-core product behind the MIXED_TF32 / MIXED_BF16 dense top,
+ * exported so that it can be tested and profiled on its own (the paper has
+ * no counterpart; it is a building block of the factorization's dense
+ * steps).  C = beta C + alpha A B^T on DEVICE float32 buffers: A is M x K
+ * with element (r, k) at A[r * rsa + k * csa], B is N x K with element
+ * (n, k) at B[n * rsb + k * csb], C is M x N column-major with leading
+ * dimension ldc >= M.  mode 0 = TF32 operands (rounded to nearest), 1 =
+ * 3xTF32 (each operand split into TF32 hi + lo, three products), 2 = BF16
+ * operands; accumulation in float32 tensor memory (tcgen05).  lower != 0
+ * writes only elements with row >= column.  Synchronises the stream.
+ * Errors: HSOLVE_ERR_ARG, HSOLVE_ERR_TIMEOUT (a bounded wait of the kernel
+ * expired), HSOLVE_ERR_CUDA. */
+hsolve_status hsolve_tc_gemm(int mode, int M, int N, int K, const float* A,
+                             int64_t rsa, int64_t csa, const float* B,
+                             int64_t rsb, int64_t csb, float* C, int64_t ldc,
+                             float alpha, float beta, int lower, void* stream);
+
 /* Statistics of the analysis and the last factorization. */
 hsolve_status hsolve_get_stats(const hsolve_handle* h, hsolve_stats* out);
 

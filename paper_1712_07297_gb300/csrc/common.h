@@ -174,6 +174,19 @@ struct ApplyRec {   // one cluster's factor, as the substitution sweeps use it
   int64_t part;     // offset of the backward partial sums (per right-hand side)
 };
 
+// Tensor-core products (kernels_tc.cu).  mode 0 = TF32, 1 = 3xTF32 (hi/lo
+// split), 2 = BF16 operands; float32 accumulation.  C = beta C + alpha A B^T
+// with A: M x K (element (r, k) at A[r * rsa + k * csa]), B: N x K likewise,
+// C column-major (ldc); lower: only tiles and elements with row >= column.
+void tc_gemm(int mode, int M, int N, int K, const float* A, int64_t rsa, int64_t csa,
+             const float* B, int64_t rsb, int64_t csb, float* C, int64_t ldc, float alpha,
+             float beta, bool lower, DevError* err, cudaStream_t st);
+// Dense top on tensor cores (float32, SPD): L into A's lower triangle, X =
+// L^{-1} (ld n); W: dense_top_tc_scratch(n) floats.
+size_t dense_top_tc_scratch(int n);
+void dense_top_tc(float* A, int64_t lda, int n, float* X, float* W, DevError* err, int level,
+                  cudaStream_t st);
+
 template <typename real>
 struct Launch {
   static void prep(const PrepTask* tasks_dev, int ntask, real* arena, real* fac,

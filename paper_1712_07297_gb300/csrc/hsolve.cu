@@ -8,6 +8,7 @@
 // hsolve_apply    Alg. 2 forward/backward substitution.
 // hsolve_solve    Sec. 5 usage: preconditioned CG / flexible GMRES in float64.
 #include <algorithm>
+#include <type_traits>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -188,6 +189,7 @@ struct hsolve_handle {
   // scratch
   DevBuf d_err;
   DevBuf ws, wsd, blob_dev, blob2, blob3, cnt;
+  DevBuf top_w;  // scratch of the tensor-core dense top
   PinnedBuf pin, pin2, pin3;
   // CUDA graphs of the substitution sweeps, one per nrhs (dropped whenever
   // the factorization or the level buffers change)
@@ -424,10 +426,21 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   const bool dense_top = (nc == 1 && sym && cur[0] > kTopOneCta);
   if (dense_top) {
     const int n = cur[0];
-    timed_lv(h, "dense_top", level, 0, [&] {
-      Launch<real>::dense_top(arena + P.off[P.find(0, 0)], P.ld[0], n, fac + oT[0],
-                              h->d_err.as<DevError>(), level, h->st);
-    });
+    if (std::is_same<real, float>::value &&
+        (h->prec == HSOLVE_MIXED_TF32 || h->prec == HSOLVE_MIXED_BF16)) {
+      // recursive Cholesky + inverse factor with tcgen05 (3xTF32) products
+      h->top_w.ensure(sizeof(float) * dense_top_tc_scratch(n));
+      timed_lv(h, "dense_top", level, 0, [&] {
+        dense_top_tc(reinterpret_cast<float*>(arena + P.off[P.find(0, 0)]), P.ld[0], n,
+                     reinterpret_cast<float*>(fac + oT[0]), h->top_w.as<float>(),
+                     h->d_err.as<DevError>(), level, h->st);
+      });
+    } else {
+      timed_lv(h, "dense_top", level, 0, [&] {
+        Launch<real>::dense_top(arena + P.off[P.find(0, 0)], P.ld[0], n, fac + oT[0],
+                                h->d_err.as<DevError>(), level, h->st);
+      });
+    }
     check_dev_error(h);
     FL.cls.push_back({0});
     FL.k[0] = 0;
@@ -1670,6 +1683,32 @@ hsolve_status hsolve_spmv(hsolve_handle* h, const double* x, double* y, int nrhs
     return set_err(h, f.code, f.msg);
   }
   return HSOLVE_OK;
+}
+
+hsolve_status hsolve_tc_gemm(int mode, int M, int N, int K, const float* A, int64_t rsa,
+                             int64_t csa, const float* B, int64_t rsb, int64_t csb, float* C,
+                             int64_t ldc, float alpha, float beta, int lower, void* stream) {
+  if (mode < 0 || mode > 2 || M < 0 || N < 0 || K < 0 || ((!A || !B) && K > 0) || !C ||
+      ldc < std::max(M, 1))
+    return HSOLVE_ERR_ARG;
+  cudaGetLastError();
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  DevError* err = nullptr;
+  if (cudaMalloc(&err, sizeof(DevError)) != cudaSuccess) return HSOLVE_ERR_OOM;
+  DevError e{};
+  hsolve_status rc = HSOLVE_OK;
+  if (cudaMemsetAsync(err, 0, sizeof(DevError), st) != cudaSuccess) rc = HSOLVE_ERR_CUDA;
+  if (rc == HSOLVE_OK) {
+    tc_gemm(mode, M, N, K, A, rsa, csa, B, rsb, csb, C, ldc, alpha, beta, lower != 0, err, st);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&e, err, sizeof(DevError), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = HSOLVE_ERR_CUDA;
+    else if (e.code != 0)
+      rc = (hsolve_status)e.code;
+  }
+  cudaFree(err);
+  return rc;
 }
 
 hsolve_status hsolve_solve(hsolve_handle* h, hsolve_krylov krylov, double tol, int maxit,

@@ -82,7 +82,12 @@ EXPORTS = {
     "hsolve_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "hsolve_last_error": (C.c_char_p, [C.c_void_p]),
     "hsolve_destroy": (None, [C.c_void_p]),
+    "hsolve_tc_gemm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64,
+                                 C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
+                                 C.c_int64, C.c_float, C.c_float, C.c_int, C.c_void_p]),
 }
+
+TC_MODES = {"tf32": 0, "3xtf32": 1, "bf16": 2}
 
 _lib = None
 
@@ -268,3 +273,23 @@ class Solver:
         arr = (PhaseTime * max(cnt.value, 1))()
         _check(lib.hsolve_get_phase_times(self.h, arr, cnt.value, C.byref(cnt)), self.h)
         return {arr[i].name.decode(): (arr[i].ms, arr[i].launches) for i in range(cnt.value)}
+
+
+def tc_gemm(mode, A, B, C_, alpha=1.0, beta=0.0, lower=False, stream=None):
+    """C_ = beta C_ + alpha A B^T on the tensor cores (hsolve_tc_gemm).
+
+    A (M x K), B (N x K): float32 CUDA tensors of any strides; C_: float32
+    CUDA tensor (M x N) stored column-major (C_.stride() == (1, ldc)).
+    mode: "tf32", "3xtf32" or "bf16"."""
+    M, K = A.shape
+    N, K2 = B.shape
+    if K2 != K or tuple(C_.shape) != (M, N) or C_.stride(0) != 1:
+        raise ValueError("tc_gemm: shapes or C layout")
+    for t in (A, B, C_):
+        if t.dtype.__str__() != "torch.float32" or not t.is_cuda:
+            raise ValueError("tc_gemm: float32 CUDA tensors")
+    st = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(load().hsolve_tc_gemm(TC_MODES[mode], M, N, K, A.data_ptr(), A.stride(0), A.stride(1),
+                                 B.data_ptr(), B.stride(0), B.stride(1), C_.data_ptr(),
+                                 max(C_.stride(1), M), float(alpha), float(beta), int(lower), st))
+    return C_

@@ -269,11 +269,12 @@ def test_cluster_qr_equals_single_cta(hs, precision):
     assert _rel(outs[1], outs[0]) < tol
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed_fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed_fp32", "mixed_tf32"])
 def test_dense_top_blocked(hs, precision):
     # a top level of more than 256 unknowns goes to the blocked multi-CTA
     # Cholesky and inverse factor (Alg. 1, dense factor when small enough);
-    # sizes not multiples of the 64-wide panels
+    # sizes not multiples of the 64-wide panels; mixed_tf32 takes the
+    # recursive tensor-core (3xTF32) top with 128-wide leaves
     p = I.poisson((16, 16, 16))
     fac = _oracle(p, 64, 1e-2, top_size=2000)
     assert any(lv.top is not None and lv.top["n"] > 256 for lv in fac.levels)
