@@ -9,7 +9,9 @@
 // hsolve_solve    Sec. 5 usage: preconditioned CG / flexible GMRES in float64.
 #include <algorithm>
 #include <type_traits>
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -226,6 +228,14 @@ struct hsolve_handle {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   std::vector<PhaseTimer> phases;
+  // next-level patterns of earlier factorizations, keyed by the pattern they
+  // were built from and the children's unknown counts
+  struct PatCache {
+    bool to_top;
+    std::vector<int> kin, m, ptr, col;
+    LevelPattern Q;
+  };
+  std::vector<PatCache> pcache;
   std::string err;
 };
 
@@ -359,6 +369,41 @@ void resolve_pending(hsolve_handle* h) {
   h->pending.clear();
 }
 
+// Run f(i) for i in [0, n) on up to 16 host threads (chunks of 16 indices);
+// f must not throw.
+template <typename F>
+void parallel_for(int n, F&& f) {
+  int nt = (int)std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
+  nt = std::min(nt, std::max(1, n / 32));
+  if (nt <= 1) {
+    for (int i = 0; i < n; i++) f(i);
+    return;
+  }
+  std::atomic<int> next(0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; t++)
+    th.emplace_back([&] {
+      for (int i0; (i0 = next.fetch_add(16)) < n;)
+        for (int i = i0; i < std::min(n, i0 + 16); i++) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
+// Host wall time of a section, added to the phase table as "host.<name>"
+// when profiling (device phases are CUDA-event times; these are not).
+struct HostTimer {
+  hsolve_handle* h;
+  const char* name;
+  std::chrono::steady_clock::time_point t0;
+  HostTimer(hsolve_handle* hh, const char* n) : h(hh), name(n), t0(std::chrono::steady_clock::now()) {}
+  ~HostTimer() {
+    if (!h->profiling) return;
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    phase_add(h, name, ms, 0);
+  }
+};
+
 void check_dev_error(hsolve_handle* h) {
   DevError e{};
   HS_CUDA(cudaMemcpyAsync(&e, h->d_err.p, sizeof(DevError), cudaMemcpyDeviceToHost, h->st));
@@ -407,7 +452,10 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     }
     fe = (fe + 3) / 4 * 4;
   }
-  FL.fac.alloc(std::max<int64_t>(fe, 4) * sizeof(real));
+  {
+    HostTimer ht(h, "host.fac_alloc");
+    FL.fac.alloc(std::max<int64_t>(fe, 4) * sizeof(real));
+  }
   h->factor_bytes += FL.fac.bytes;
   real* fac = FL.fac.as<real>();
   DevBuf d_rank;
@@ -421,6 +469,44 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   std::vector<int64_t> vmap;
   std::vector<int> fillcols(nc, 0), fillw(nc, 0), nzcols(nc, -1);
   FL.cls.clear();
+  // rank-independent part of every cluster's tasks, built in parallel: its
+  // pattern row without the diagonal (neighbour or fill block, both block
+  // offsets) and, for every ordered pair of its neighbours, the offset of
+  // their block (the Schur-complement targets)
+  struct NbPre {
+    int j, kind;
+    int64_t p_sj, p_js;
+  };
+  std::vector<std::vector<NbPre>> pre_nb(nc);
+  std::vector<std::vector<int64_t>> pre_sb(nc);
+  {
+    HostTimer ht(h, "host.prepass");
+    parallel_for(nc, [&](int s) {
+      if (P.m[s] == 0) return;
+      auto& L = pre_nb[s];
+      int nn = 0;
+      for (int p = P.ptr[s]; p < P.ptr[s + 1]; p++) {
+        const int j = P.col[p];
+        if (j == s) continue;
+        L.push_back({j, (int)P.kind[p], P.off[p], P.off[P.find(j, s)]});
+        nn += P.kind[p] == 1;
+      }
+      auto& sb = pre_sb[s];
+      sb.resize((size_t)nn * nn);
+      int a = 0;
+      for (auto& ea : L) {
+        if (ea.kind != 1) continue;
+        int b = 0;
+        for (auto& eb : L) {
+          if (eb.kind != 1) continue;
+          const int64_t q = P.find(ea.j, eb.j);
+          sb[(size_t)a * nn + b] = q < 0 ? -1 : P.off[q];
+          b++;
+        }
+        a++;
+      }
+    });
+  }
   // a single large SPD cluster (the dense top of Alg. 1) goes to the blocked
   // multi-CTA Cholesky and inverse factor: E_s = I, k = 0, no neighbours
   const bool dense_top = (nc == 1 && sym && cur[0] > kTopOneCta);
@@ -454,6 +540,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     h->apply_bytes += (int64_t)sizeof(real) * 2 * ((int64_t)n * n + 2 * (int64_t)n);
   }
   for (size_t c = 0; c < P.classes.size() && !dense_top; c++) {
+    std::unique_ptr<HostTimer> hb(new HostTimer(h, "host.build"));
     std::vector<int> S;
     for (int s : P.classes[c])
       if (cur[s] > 0) S.push_back(s);
@@ -475,14 +562,14 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       const int s = S[t];
       const int m = cur[s];
       maxm = std::max(maxm, m);
-      struct Nb { int j, w; int64_t p_sj, p_js; };
+      struct Nb { int j, w; int64_t p_sj, p_js; int ia; };
       std::vector<Nb> N, W;
-      for (int p = P.ptr[s]; p < P.ptr[s + 1]; p++) {
-        int j = P.col[p];
-        if (j == s || cur[j] == 0) continue;
-        int64_t pj = P.find(j, s);
-        Nb e{j, cur[j], P.off[p], P.off[pj]};
-        if (P.kind[p] == 1) N.push_back(e);
+      int nn_all = 0;  // neighbours in the pattern (index base of pre_sb)
+      for (auto& e0 : pre_nb[s]) {
+        const int ia = e0.kind == 1 ? nn_all++ : -1;
+        if (cur[e0.j] == 0) continue;
+        Nb e{e0.j, cur[e0.j], e0.p_sj, e0.p_js, ia};
+        if (e0.kind == 1) N.push_back(e);
         else W.push_back(e);
       }
       int nw = 0, nwf = 0;
@@ -617,11 +704,12 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         sc.Q = oY[s];
         sc.map = ncol0;  // the A_sN runs: one per neighbour, colstart = its offset
         sc.base = (int64_t)sbase.size();
+        const auto& sb = pre_sb[s];
         for (int a = 0; a < (int)N.size(); a++)
           for (int b = 0; b < (int)N.size(); b++) {
-            int64_t p = P.find(N[a].j, N[b].j);
-            if (p < 0) throw Fail(HSOLVE_ERR_CUDA, "internal: missing Schur target block");
-            sbase.push_back(P.off[p]);
+            const int64_t o = sb[(size_t)N[a].ia * nn_all + N[b].ia];
+            if (o < 0) throw Fail(HSOLVE_ERR_CUDA, "internal: missing Schur target block");
+            sbase.push_back(o);
           }
         sc.ldn = (int64_t)sld.size();
         for (auto& e : N) sld.push_back(P.ld[e.j]);
@@ -646,6 +734,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     h->ws.ensure(std::max<int64_t>(ws_e, 4) * sizeof(real));
     h->wsd.ensure(std::max<int64_t>(wsd_e, 4) * sizeof(double));
     char* d = upload_blob(h, b);
+    hb.reset();
     real* ws = h->ws.as<real>();
     const PrepTask* d_prep = reinterpret_cast<const PrepTask*>(d + o_prep);
     const Seg* d_segs = reinterpret_cast<const Seg*>(d + o_segs);
@@ -678,9 +767,15 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
                                h->cnt.as<int>(), h->st);
       });
       std::vector<int> cnt(qrt.size());
-      HS_CUDA(cudaMemcpyAsync(cnt.data(), h->cnt.p, sizeof(int) * cnt.size(),
-                              cudaMemcpyDeviceToHost, h->st));
-      HS_CUDA(cudaStreamSynchronize(h->st));
+      {
+        HostTimer ht(h, "host.count_copy");
+        HS_CUDA(cudaMemcpyAsync(cnt.data(), h->cnt.p, sizeof(int) * cnt.size(),
+                                cudaMemcpyDeviceToHost, h->st));
+      }
+      {
+        HostTimer ht(h, "host.wait_count");
+        HS_CUDA(cudaStreamSynchronize(h->st));
+      }
       for (size_t i = 0; i < qrt.size(); i++) nzcols[qrt[i].s] = cnt[i];
       const int nzmax = std::max(1, *std::max_element(cnt.begin(), cnt.end()));
       int CL = Launch<real>::qr_cluster_size(qm, nzmax);
@@ -769,8 +864,14 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     });
     // ---- ranks of this class (the next class's neighbour widths need them)
     std::vector<int> kk(nc);
-    HS_CUDA(cudaMemcpyAsync(kk.data(), rank, sizeof(int) * nc, cudaMemcpyDeviceToHost, h->st));
-    check_dev_error(h);  // synchronises the stream
+    {
+      HostTimer ht(h, "host.rank_copy");
+      HS_CUDA(cudaMemcpyAsync(kk.data(), rank, sizeof(int) * nc, cudaMemcpyDeviceToHost, h->st));
+    }
+    {
+      HostTimer ht(h, "host.wait_rank");
+      check_dev_error(h);  // synchronises the stream
+    }
     for (int s : S) {
       FL.k[s] = kk[s];
       cur[s] = kk[s];
@@ -804,6 +905,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     }
   }
   // ---- apply records and maps for this level
+  HostTimer ht_end(h, "host.level_end");
   Blob b;
   FL.recs.alloc(sizeof(ApplyRec) * std::max(nc, 1));
   FL.vmap.alloc(sizeof(int64_t) * std::max<size_t>(vmap.size(), 1));
@@ -861,21 +963,35 @@ void build_next(hsolve_handle* h, FLevel& FL, const real* arena, std::unique_ptr
     ro[a] = Q.m[I];
     Q.m[I] += kin[a];
   }
-  std::vector<std::vector<int>> adj(Q.nclu);
-  for (int a = 0; a < nc; a++) {
-    if (kin[a] == 0) continue;
-    for (int p = P.ptr[a]; p < P.ptr[a + 1]; p++) {
-      int b = P.col[p];
-      if (kin[b] == 0) continue;
-      int I = parent(a), J = parent(b);
-      if (I != J) adj[I].push_back(J);
+  // the next pattern (and its colouring) depends only on this pattern and on
+  // which children keep unknowns and how many: reuse it when a previous
+  // factorization met the same (a refactorization with the same eps)
+  hsolve_handle::PatCache* hit = nullptr;
+  for (auto& pc : h->pcache)
+    if (pc.to_top == to_top && pc.kin == kin && pc.m == P.m && pc.col == P.col &&
+        pc.ptr == P.ptr)
+      hit = &pc;
+  if (hit) {
+    Q = hit->Q;
+  } else {
+    std::vector<std::vector<int>> adj(Q.nclu);
+    for (int a = 0; a < nc; a++) {
+      if (kin[a] == 0) continue;
+      for (int p = P.ptr[a]; p < P.ptr[a + 1]; p++) {
+        int b = P.col[p];
+        if (kin[b] == 0) continue;
+        int I = parent(a), J = parent(b);
+        if (I != J) adj[I].push_back(J);
+      }
     }
+    for (auto& v : adj) {
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+    build_level_pattern(Q, adj);
+    if (h->pcache.size() >= 32) h->pcache.erase(h->pcache.begin());
+    h->pcache.push_back({to_top, kin, P.m, P.ptr, P.col, Q});
   }
-  for (auto& v : adj) {
-    std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
-  }
-  build_level_pattern(Q, adj);
   out_arena.alloc(Q.arena_elems * sizeof(real));
   HS_CUDA(cudaMemsetAsync(out_arena.p, 0, Q.arena_elems * sizeof(real), h->st));
   std::vector<CopyTask> tasks;
@@ -922,7 +1038,10 @@ void build_next(hsolve_handle* h, FLevel& FL, const real* arena, std::unique_ptr
 
 template <typename real>
 void factor_impl(hsolve_handle* h, double eps) {
-  h->F.clear();
+  {
+    HostTimer ht(h, "host.clear");
+    h->F.clear();
+  }
   h->factor_flops = h->schur_flops = h->prep_flops = h->gemm_flops = h->qr_flops = 0;
   h->apply_bytes = h->factor_bytes = h->block_bytes = 0;
   h->launches = 0;
@@ -959,7 +1078,10 @@ void factor_impl(hsolve_handle* h, double eps) {
       std::unique_ptr<FLevel> nxt;
       DevBuf narena;
       std::vector<int> kin(P.m.begin(), P.m.end());
-      build_next<real>(h, *cur, arena.as<real>(), nxt, narena, true, kin);
+      {
+        HostTimer ht(h, "host.build_next");
+        build_next<real>(h, *cur, arena.as<real>(), nxt, narena, true, kin);
+      }
       // the merge level itself has no factors: mark it as a pass-through
       cur->cls.clear();
       cur->cls_off.assign(1, 0);
@@ -983,7 +1105,10 @@ void factor_impl(hsolve_handle* h, double eps) {
     std::unique_ptr<FLevel> nxt;
     DevBuf narena;
     std::vector<int> kin = cur->k;
-    build_next<real>(h, *cur, arena.as<real>(), nxt, narena, false, kin);
+    {
+      HostTimer ht(h, "host.build_next");
+      build_next<real>(h, *cur, arena.as<real>(), nxt, narena, false, kin);
+    }
     h->F.push_back(std::move(cur));
     cur = std::move(nxt);
     arena = std::move(narena);
