@@ -46,11 +46,18 @@ typedef enum {
 
 typedef enum {
   HSOLVE_FP64 = 0,        /* every factor block and product in float64 */
-  HSOLVE_MIXED_FP32 = 1,  /* float32 blocks, float32 SIMT products,
-                             float64 rank decision, float64 outer Krylov */
-  HSOLVE_MIXED_TF32 = 2,  /* as MIXED_FP32, Schur-complement products on
-                             tcgen05 tensor cores (TF32 in, FP32 accumulate) */
-  HSOLVE_MIXED_BF16 = 3   /* as MIXED_TF32 with BF16 operands */
+  HSOLVE_MIXED_FP32 = 1,  /* float32 blocks and float32 SIMT products, except
+                             the dense top: a recursive Cholesky whose
+                             products run on tcgen05 tensor cores as 3xTF32
+                             (float32-level accuracy); float64 rank
+                             decision, float64 outer Krylov */
+  HSOLVE_MIXED_TF32 = 2,  /* as MIXED_FP32, with the Schur-complement products
+                             (Eq. elim) on tcgen05 tensor cores, TF32
+                             operands and float32 accumulation */
+  HSOLVE_MIXED_BF16 = 3,  /* as MIXED_TF32 with BF16 Schur operands */
+  HSOLVE_MIXED_3XTF32 = 4 /* as MIXED_TF32 with 3xTF32 Schur products (each
+                             operand split into TF32 hi + lo: float32-level
+                             accuracy on the tensor cores) */
 } hsolve_precision;
 
 typedef enum { HSOLVE_PCG = 0, HSOLVE_GMRES = 1 } hsolve_krylov;

@@ -184,6 +184,11 @@ void tc_gemm(int mode, int M, int N, int K, const float* A, int64_t rsa, int64_t
 // Dense top on tensor cores (float32, SPD): L into A's lower triangle, X =
 // L^{-1} (ld n); W: dense_top_tc_scratch(n) floats.
 size_t dense_top_tc_scratch(int n);
+// Schur-complement update of a colour class (the SIMT schur launch's
+// arguments) with tensor-core products in the given mode.
+void schur_tc(int mode, const SchurTask* tasks, int ntask, int maxnw, const float* fac,
+              float* arena, const Seg* segs, const int64_t* base, const int* ldn, const int* rank,
+              DevError* err, cudaStream_t st);
 void dense_top_tc(float* A, int64_t lda, int n, float* X, float* W, DevError* err, int level,
                   cudaStream_t st);
 

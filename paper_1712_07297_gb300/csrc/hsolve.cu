@@ -240,6 +240,15 @@ struct hsolve_handle {
 };
 
 namespace {
+// tensor-core operand mode of the Schur products (tc_gemm modes), -1: SIMT
+int tc_schur_mode(int prec) {
+  switch (prec) {
+    case HSOLVE_MIXED_TF32: return 0;
+    case HSOLVE_MIXED_3XTF32: return 1;
+    case HSOLVE_MIXED_BF16: return 2;
+    default: return -1;
+  }
+}
 constexpr int kNumSMs = 152;  // SMs of one GB300 (2 dies x 76)
 // the equilibration S by original index, or null when A is factored itself
 const double* hscale(const hsolve_handle* h) {
@@ -512,9 +521,9 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   const bool dense_top = (nc == 1 && sym && cur[0] > kTopOneCta);
   if (dense_top) {
     const int n = cur[0];
-    if (std::is_same<real, float>::value &&
-        (h->prec == HSOLVE_MIXED_TF32 || h->prec == HSOLVE_MIXED_BF16)) {
-      // recursive Cholesky + inverse factor with tcgen05 (3xTF32) products
+    if (std::is_same<real, float>::value) {
+      // float32 modes: recursive Cholesky + inverse factor with tcgen05
+      // 3xTF32 products (float32-level accuracy)
       h->top_w.ensure(sizeof(float) * dense_top_tc_scratch(n));
       timed_lv(h, "dense_top", level, 0, [&] {
         dense_top_tc(reinterpret_cast<float*>(arena + P.off[P.find(0, 0)]), P.ld[0], n,
@@ -857,10 +866,17 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
                             maxw_seg, ws, arena, rank, h->st);
     });
     timed_lv(h, "schur", level, 1, [&] {
-      Launch<real>::schur(reinterpret_cast<const SchurTask*>(d + o_sch), (int)sch.size(), maxnw,
-                          fac, arena, d_segs,
-                          reinterpret_cast<const int64_t*>(d + o_sbase),
-                          reinterpret_cast<const int*>(d + o_sld), rank, h->st);
+      const int tm = tc_schur_mode(h->prec);
+      if (std::is_same<real, float>::value && tm >= 0)
+        schur_tc(tm, reinterpret_cast<const SchurTask*>(d + o_sch), (int)sch.size(), maxnw,
+                 reinterpret_cast<const float*>(fac), reinterpret_cast<float*>(arena), d_segs,
+                 reinterpret_cast<const int64_t*>(d + o_sbase),
+                 reinterpret_cast<const int*>(d + o_sld), rank, h->d_err.as<DevError>(), h->st);
+      else
+        Launch<real>::schur(reinterpret_cast<const SchurTask*>(d + o_sch), (int)sch.size(),
+                            maxnw, fac, arena, d_segs,
+                            reinterpret_cast<const int64_t*>(d + o_sbase),
+                            reinterpret_cast<const int*>(d + o_sld), rank, h->st);
     });
     // ---- ranks of this class (the next class's neighbour widths need them)
     std::vector<int> kk(nc);
@@ -1726,7 +1742,7 @@ hsolve_status hsolve_analyze(const hsolve_csr* A, const double* coords, int dim,
 hsolve_status hsolve_factor(hsolve_handle* h, double eps, hsolve_precision prec) {
   if (!h) return HSOLVE_ERR_ARG;
   cudaGetLastError();  // a stale error of another runtime user is not ours
-  if (!(eps >= 0.0) || prec < HSOLVE_FP64 || prec > HSOLVE_MIXED_BF16)
+  if (!(eps >= 0.0) || prec < HSOLVE_FP64 || prec > HSOLVE_MIXED_3XTF32)
     return set_err(h, HSOLVE_ERR_ARG, "bad eps or precision");
   h->factored = false;
   h->drop_graphs();

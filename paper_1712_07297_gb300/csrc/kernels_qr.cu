@@ -7,9 +7,9 @@
 // memory instead of L2.  Per step the CTAs agree on the pivot through
 // distributed shared memory: the largest remaining column norm over the
 // cluster, then the lowest original column index among the columns within
-// 1e-10 of it (the tie rule of the single-CTA path); the owner CTA forms the
-// reflector, every CTA reads it from the owner's shared memory and updates
-// its columns.  Three cluster barriers per step; every CTA takes the same
+// 1e-10 of it (the tie rule of the single-CTA path); every CTA forms the
+// reflector from the pivot column in the owner's shared memory and updates
+// its columns.  Two cluster barriers per step; every CTA takes the same
 // branches (its decisions use the same exchanged values), so the barriers
 // always match.
 //
@@ -38,15 +38,14 @@ constexpr int kMaxGrid = 1 << 20;
 // Dynamic shared memory of one CTA: every array starts on a 16-byte boundary
 // (the same computation sizes the launch and carves the buffer).
 struct QrSmem {
-  size_t G, nrm, oidx, tpos, vbuf, vloc, total;
+  size_t G, nrm, oidx, tpos, vloc, total;
   __host__ __device__ static size_t al(size_t b) { return (b + 15) / 16 * 16; }
   __host__ __device__ QrSmem(int ldsm, int cc, int sz) {
     G = 0;
     nrm = G + al((size_t)ldsm * cc * sz);
     oidx = nrm + al((size_t)cc * sizeof(double));
     tpos = oidx + al((size_t)cc * sizeof(int));
-    vbuf = tpos + al((size_t)256 * sizeof(int));
-    vloc = vbuf + al((size_t)ldsm * sz);
+    vloc = tpos + al((size_t)256 * sizeof(int));
     total = vloc + al((size_t)ldsm * sz);
   }
 };
@@ -54,7 +53,6 @@ struct QrSmem {
 struct Exchange {
   double val;      // largest local squared norm
   double candnrm;  // squared norm of the local candidate
-  double tau;      // owner: 2 / v^T v of the step's reflector
   int cand;        // lowest original index among the local candidates
   int loc;         // local column of the candidate
 };
@@ -84,18 +82,6 @@ __device__ double block_max(double v, double* red) {
   return r;
 }
 
-__device__ int block_min(int v, int* red) {
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = min(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
-  }
-  int r = red[0];
-  __syncthreads();
-  return r;
-}
-
 template <typename real>
 __global__ void __launch_bounds__(256)
 qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ arena,
@@ -108,7 +94,6 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
   const PrepTask tk = tasks[blockIdx.x / CL];
   const int m = tk.m, c = tk.ncolG;
   __shared__ double red_d[256];
-  __shared__ int red_i[256];
   __shared__ Exchange xch;
   extern __shared__ __align__(16) unsigned char dsm[];
   const QrSmem lay(ldsm, ccmax, (int)sizeof(real));
@@ -116,8 +101,7 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
   double* nrm = reinterpret_cast<double*>(dsm + lay.nrm);
   int* oidx = reinterpret_cast<int*>(dsm + lay.oidx);
   int* tpos = reinterpret_cast<int*>(dsm + lay.tpos);
-  real* vbuf = reinterpret_cast<real*>(dsm + lay.vbuf);  // the owner's reflector
-  real* vloc = reinterpret_cast<real*>(dsm + lay.vloc);  // this CTA's copy
+  real* vloc = reinterpret_cast<real*>(dsm + lay.vloc);  // the step's reflector
 
   // per-cluster outputs (same layout as the per-cluster kernel)
   double* nrm2_g = wsd_all + tk.wsd;
@@ -247,31 +231,28 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
     const double r = s_r;
     if (j == 0) r11 = r;
     if (r <= floor || (eps > 0.0 && r <= eps * r11) || j >= kmax) break;
-    // 3. the owner forms the reflector v = x - beta e1, beta = -sign(x0) ||x||
-    if (cr == owner) {
-      const int loc = xch.loc;
-      const double x0 = (double)Gs[j + (int64_t)loc * ldsm];
-      const double beta = (x0 >= 0.0) ? -r : r;
-      const double tj = (r > 0.0) ? 1.0 / (r * (r + fabs(x0))) : 0.0;
-      for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
-        const real v = (i == j) ? (real)(x0 - beta) : Gs[i + (int64_t)loc * ldsm];
-        vbuf[i] = v;
-        W_G[i + (int64_t)j * m] = v;
-      }
-      if (threadIdx.x == 0) {
-        xch.tau = tj;
-        tau_g[j] = (real)tj;
-        rsign_g[j] = beta < 0.0 ? real(-1) : real(1);
-        nrm[loc] = -1.0;  // used: out of every later step
-      }
+    // 3. every CTA forms the reflector v = x - beta e1, beta = -sign(x0) ||x||
+    //    from the pivot column in the owner's shared memory (read through
+    //    distributed shared memory; that column is never written again, so
+    //    no further cluster barrier is needed); the owner also stores it
+    const int oloc = cl.map_shared_rank(&xch, owner)->loc;
+    const real* ocol = cl.map_shared_rank(Gs, owner) + (int64_t)oloc * ldsm;
+    const double x0 = (double)ocol[j];
+    const double beta = (x0 >= 0.0) ? -r : r;
+    const real tj = (real)((r > 0.0) ? 1.0 / (r * (r + fabs(x0))) : 0.0);
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+      const real v = (i == j) ? (real)(x0 - beta) : ocol[i];
+      vloc[i] = v;
+      if (cr == owner) W_G[i + (int64_t)j * m] = v;
     }
-    cl.sync();
+    if (cr == owner && threadIdx.x == 0) {
+      tau_g[j] = tj;
+      rsign_g[j] = beta < 0.0 ? real(-1) : real(1);
+      nrm[oloc] = -1.0;  // used: out of every later step
+    }
+    __syncthreads();
     // 4. every CTA applies the reflector to its remaining columns and
     //    recomputes their squared norms over rows j+1..m
-    const real* ov = cl.map_shared_rank(vbuf, owner);
-    const real tj = (real)cl.map_shared_rank(&xch, owner)->tau;
-    for (int i = j + threadIdx.x; i < m; i += blockDim.x) vloc[i] = ov[i];
-    __syncthreads();
     for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
       if (nrm[t] < 0.0) continue;
       real* col = Gs + (int64_t)t * ldsm;

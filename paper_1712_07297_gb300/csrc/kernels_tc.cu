@@ -163,10 +163,66 @@ struct TcMode {
 // Stage rows [r0, r0 + 128) x K-chunk [k0, k0 + kKChunk) of an operand
 // (element (r, k) at P[r * rs + k * cs]) into tile(s) at `dst`.  Thread t
 // takes row t: 128 bytes of K per row, written as 16-byte vectors.
+// Convert and store the EQ consecutive K-elements x[0..EQ) of row r at
+// 16-byte core row (r, q) (and the lo part for 3xTF32).
+template <int MODE, int EQ>
+__device__ __forceinline__ void store_quad(const float* x, int r, int q, unsigned char* dst) {
+  if (MODE == 2) {
+    uint32_t w[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * t], x[2 * t + 1]);
+      w[t] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    *reinterpret_cast<uint4*>(dst + core_off(r, q * 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {
+    float hi[4], lo[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      hi[t] = tf32_round(x[t]);
+      lo[t] = tf32_round(x[t] - hi[t]);
+    }
+    *reinterpret_cast<float4*>(dst + core_off(r, q * 16)) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    if (MODE == 1)
+      *reinterpret_cast<float4*>(dst + kTileBytes + core_off(r, q * 16)) =
+          make_float4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
+// Staging of an operand whose K elements are contiguous (cs == 1): the
+// tile's (row, 16-byte quad) items go 8 rows x 4 quads per warp and
+// instruction, so a load touches 8 lines (not 32) and the 16-byte shared
+// stores of 8 consecutive lanes fill 8 different rows of one core matrix
+// (no bank conflicts).
+template <int MODE>
+__device__ __forceinline__ void stage_operand_kc(const float* __restrict__ P, int64_t rs, int rows,
+                                                 int K, int r0, int k0, unsigned char* dst) {
+  constexpr int EQ = TcMode<MODE>::kKChunk / 8;  // elements per 16-byte quad
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rr = lane & 7, qa = lane >> 3;
+#pragma unroll 2
+  for (int it = 0; it < 8; it++) {
+    const int pi = it * 4 + warp;  // (row group of 8, half of the 8 quads)
+    const int r = (pi >> 1) * 8 + rr, q = (pi & 1) * 4 + qa;
+    const int gr = r0 + r;
+    float x[EQ];
+#pragma unroll
+    for (int t = 0; t < EQ; t++) {
+      const int gk = k0 + q * EQ + t;
+      x[t] = (gr < rows && gk < K) ? P[(int64_t)gr * rs + gk] : 0.0f;
+    }
+    store_quad<MODE, EQ>(x, r, q, dst);
+  }
+}
+
 template <int MODE>
 __device__ __forceinline__ void stage_operand(const float* __restrict__ P, int64_t rs, int64_t cs,
                                               int rows, int K, int r0, int k0, unsigned char* dst) {
   using M = TcMode<MODE>;
+  if (cs == 1 && rs != 1) {
+    stage_operand_kc<MODE>(P, rs, rows, K, r0, k0, dst);
+    return;
+  }
   const int r = threadIdx.x;
   const int gr = r0 + r;
   float x[M::kKChunk];
@@ -308,26 +364,175 @@ tc_gemm_kernel(int M, int N, int K, const float* __restrict__ A, int64_t rsa, in
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
 }
 
+// ---- Schur-complement update of a colour class on the tensor cores
+// (Eq. elim): for every task, A_NN -= P^T Q with P = B_L^T, Q = B_R stored as
+// f x nw (rows k.. of the cluster's Y storage, ld m, f = m - rank).  Grid
+// (column tile, row tile, task); the 128 x 128 accumulator tile is
+// subtracted from the neighbour blocks it maps to (runs of the neighbour
+// columns, block bases and leading dimensions as in the SIMT update).  The
+// blocks of one colour class are disjoint, so no two CTAs write the same
+// element.
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads)
+schur_tc_kernel(const SchurTask* __restrict__ tasks, const float* __restrict__ fac,
+                float* __restrict__ arena, const Seg* __restrict__ segs,
+                const int64_t* __restrict__ base, const int* __restrict__ ldn,
+                const int* __restrict__ rank, DevError* err) {
+  using MD = TcMode<MODE>;
+  const SchurTask tk = tasks[blockIdx.z];
+  const int k = rank[tk.s];
+  const int f = tk.m - k;
+  const int N = tk.nw;
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+  if (f <= 0 || i0 >= N || j0 >= N) return;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  __shared__ int rblk[TM], rloc[TM], cblk[TN], cloc[TN];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* stages = tc_smem + ((1024 - (smem_u32(tc_smem) & 1023)) & 1023);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // neighbour run and local index of every row / column of the tile
+  const Seg* sg = segs + tk.map;
+  for (int e = threadIdx.x; e < TM + TN; e += blockDim.x) {
+    const int r = (e < TM) ? i0 + e : j0 + (e - TM);
+    int a = 0, lr = 0;
+    if (r < N) {
+      int lo = 0, hi = tk.nb - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sg[mid].colstart <= r) lo = mid;
+        else hi = mid - 1;
+      }
+      a = lo;
+      lr = r - sg[lo].colstart;
+    }
+    if (e < TM) {
+      rblk[e] = a;
+      rloc[e] = lr;
+    } else {
+      cblk[e - TM] = a;
+      cloc[e - TM] = lr;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const float* P = fac + tk.P + k;
+  const float* Q = fac + tk.Q + k;
+  const int64_t ld = tk.m;
+  const int nchunk = (f + MD::kKChunk - 1) / MD::kKChunk;
+  for (int c = 0; c < nchunk; c++) {
+    const int s = c & 1;
+    unsigned char* st = stages + s * MD::kStageBytes;
+    if (c >= 2 && !mbar_wait(&bar[s], ((c - 2) >> 1) & 1)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    stage_operand<MODE>(P, ld, 1, N, f, i0, c * MD::kKChunk, st);
+    stage_operand<MODE>(Q, ld, 1, N, f, j0, c * MD::kKChunk, st + MD::kTiles * kTileBytes);
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + MD::kTiles * kTileBytes);
+#pragma unroll
+      for (int kk = 0; kk < MD::kKChunk / MD::kKMma; kk++) {
+        const uint32_t off = kk * 2 * kLBO;
+        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+        tc_mma<MD::kKind>(tmem, smem_desc(a0 + off, kLBO, kSBO), smem_desc(b0 + off, kLBO, kSBO),
+                          MD::kIdesc, acc);
+        if (MODE == 1) {
+          tc_mma<MD::kKind>(tmem, smem_desc(a0 + off, kLBO, kSBO),
+                            smem_desc(b0 + kTileBytes + off, kLBO, kSBO), MD::kIdesc, 1u);
+          tc_mma<MD::kKind>(tmem, smem_desc(a0 + kTileBytes + off, kLBO, kSBO),
+                            smem_desc(b0 + off, kLBO, kSBO), MD::kIdesc, 1u);
+        }
+      }
+      tc_commit(&bar[s]);
+    }
+  }
+  if (!abort_flag) {
+    const int cl = nchunk - 1;
+    if (!mbar_wait(&bar[cl & 1], (cl >> 1) & 1)) abort_flag = 1;
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (!abort_flag) {
+    const int ii = warp * 32 + lane, gi = i0 + ii;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    const int64_t* bs = base + tk.base;
+    const int* ldv = ldn + tk.ldn;
+    const int a = rblk[ii], lr = rloc[ii];
+    const int64_t lda = ldv[a];
+    for (int jc = 0; jc < TN; jc += 32) {
+      float v[32];
+      tmem_ld32(tl + jc, v);
+      if (gi < N) {
+#pragma unroll 4
+        for (int q = 0; q < 32; q++) {
+          const int jj = jc + q;
+          if (j0 + jj < N) arena[bs[a * tk.nb + cblk[jj]] + lr + cloc[jj] * lda] -= v[q];
+        }
+      }
+    }
+  } else if (threadIdx.x == 0 && err) {
+    if (atomicCAS(&err->code, 0, (int)HSOLVE_ERR_TIMEOUT) == 0) {
+      err->cluster = tk.s;
+      err->level = -1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+}
+
 // ---- dense top leaves: Cholesky and inverse factor of an n <= 128 block on
 // one CTA (lower triangle of A in, L into A's lower triangle, X = L^{-1}
 // into X with zeros above the diagonal)
 constexpr int kLeaf = 128;
 
-__global__ void __launch_bounds__(256)
+// 256 threads as a 16 x 16 grid; thread (tr, tc) keeps the elements (tr +
+// 16 a, tc + 16 b), a, b < 8, of the factor (and then of the inverse) in
+// registers, so a step reads 16 broadcast values from shared memory and
+// updates up to 64 registers; two barriers per step.  The pivots come from a
+// shared copy of the trailing diagonal updated alongside.
+__global__ void __launch_bounds__(256, 1)
 chol_inv_leaf_kernel(float* A, int64_t lda, float* X, int64_t ldx, int n, DevError* err,
                      int level) {
+  constexpr int G = 16, R8 = kLeaf / G;
   extern __shared__ float leaf_smem[];
   const int ld = kLeaf + 1;
-  float* S = leaf_smem;            // L (column-major, ld)
-  float* Y = leaf_smem + ld * kLeaf;  // L^{-1}
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j < n; j += nw)
-    for (int i = lane; i < n; i += 32) S[i + j * ld] = (i >= j) ? A[i + (int64_t)j * lda] : 0.f;
+  float* Ls = leaf_smem;                // L, column-major (for the inverse)
+  float* vec = leaf_smem + ld * kLeaf;  // the step's column / row
+  __shared__ float diag[kLeaf];         // the trailing diagonal (the pivots)
+  const int tr = threadIdx.x % G, tc = threadIdx.x / G;
+  float R[R8][R8];
+#pragma unroll
+  for (int a = 0; a < R8; a++)
+#pragma unroll
+    for (int b = 0; b < R8; b++) {
+      const int i = tr + G * a, l = tc + G * b;
+      R[a][b] = (i < n && l < n && i >= l) ? A[i + (int64_t)l * lda] : 0.f;
+    }
+  for (int t = threadIdx.x; t < n; t += blockDim.x) diag[t] = A[t + (int64_t)t * lda];
   __syncthreads();
-  // right-looking Cholesky, one barrier per step (column j-1 finished in step j)
-  float rprev = 0.f;
+  // ---- Cholesky, right-looking: scale column j, then update the trailing part
   for (int j = 0; j < n; j++) {
-    const float d = S[j + j * ld];
+    const float d = diag[j];
     if (!(d > 0.f)) {
       if (threadIdx.x == 0 && atomicCAS(&err->code, 0, (int)HSOLVE_ERR_NOT_SPD) == 0) {
         err->cluster = 0;
@@ -335,40 +540,97 @@ chol_inv_leaf_kernel(float* A, int64_t lda, float* X, int64_t ldx, int n, DevErr
       }
       return;  // uniform
     }
-    const float invd = 1.f / d;
-    if (j > 0)
-      for (int i = j + threadIdx.x; i < n; i += blockDim.x) S[i + (j - 1) * ld] *= rprev;
-    for (int l = j + 1 + warp; l < n; l += nw) {
-      const float alj = S[l + j * ld] * invd;
-      for (int i = l + lane; i < n; i += 32) S[i + l * ld] -= S[i + j * ld] * alj;
+    const float rs = rsqrtf(d);
+    const int jb = j / G;
+    if (tc == j % G) {
+#pragma unroll
+      for (int a = 0; a < R8; a++) {
+        const int i = tr + G * a;
+#pragma unroll
+        for (int b = 0; b < R8; b++)
+          if (b == jb && i >= j && i < n) {
+            R[a][b] = (i == j) ? d * rs : R[a][b] * rs;
+            vec[i] = R[a][b];
+          }
+      }
     }
     __syncthreads();
-    if (j > 0 && threadIdx.x == 0) S[(j - 1) + (j - 1) * ld] = 1.f / rprev;
-    rprev = 1.f / sqrtf(d);
+    float ci[R8], cl[R8];
+#pragma unroll
+    for (int a = 0; a < R8; a++) {
+      const int i = tr + G * a;
+      ci[a] = (i > j && i < n) ? vec[i] : 0.f;
+    }
+#pragma unroll
+    for (int b = 0; b < R8; b++) {
+      const int l = tc + G * b;
+      cl[b] = (l > j && l < n) ? vec[l] : 0.f;
+    }
+#pragma unroll
+    for (int a = 0; a < R8; a++)
+#pragma unroll
+      for (int b = 0; b < R8; b++) {
+        const int i = tr + G * a, l = tc + G * b;
+        if (i >= l) R[a][b] -= ci[a] * cl[b];
+      }
+    // the pivots of the later steps
+    for (int t = j + 1 + threadIdx.x; t < n; t += blockDim.x) diag[t] -= vec[t] * vec[t];
+    __syncthreads();
   }
-  if (threadIdx.x == 0) S[(n - 1) + (n - 1) * ld] = 1.f / rprev;
-  // Y = L^{-1}: identity, then forward substitution on all columns in step
-  for (int j = warp; j < n; j += nw)
-    for (int i = lane; i < n; i += 32) Y[i + j * ld] = (i == j) ? 1.f : 0.f;
+  // ---- L to shared memory and global; R becomes Y = L^{-1}, from I
+#pragma unroll
+  for (int a = 0; a < R8; a++)
+#pragma unroll
+    for (int b = 0; b < R8; b++) {
+      const int i = tr + G * a, l = tc + G * b;
+      if (i < n && l < n) {
+        Ls[i + l * ld] = (i >= l) ? R[a][b] : 0.f;
+        if (i >= l) A[i + (int64_t)l * lda] = R[a][b];
+      }
+      R[a][b] = (i == l && i < n) ? 1.f : 0.f;
+    }
   __syncthreads();
-  float dprev = 1.f;
+  // forward substitution on all columns at once: step i scales row i by
+  // 1 / l_ii, then y_rc -= l_ri y_ic for r > i, c <= i
   for (int i = 0; i < n; i++) {
-    const float di = 1.f / S[i + i * ld];
-    if (i > 0)
-      for (int c = threadIdx.x; c < i; c += blockDim.x) Y[(i - 1) + c * ld] *= dprev;
-    for (int c = warp; c <= i; c += nw) {
-      const float xic = Y[i + c * ld] * di;
-      for (int r = i + 1 + lane; r < n; r += 32) Y[r + c * ld] -= S[r + i * ld] * xic;
+    const float di = 1.f / Ls[i + i * ld];
+    const int ib = i / G;
+    if (tr == i % G) {
+#pragma unroll
+      for (int a = 0; a < R8; a++)
+#pragma unroll
+        for (int b = 0; b < R8; b++) {
+          const int c = tc + G * b;
+          if (a == ib && c <= i) {
+            R[a][b] *= di;
+            vec[c] = R[a][b];
+          }
+        }
     }
-    dprev = di;
+    __syncthreads();
+    float lr[R8], yc[R8];
+#pragma unroll
+    for (int a = 0; a < R8; a++) {
+      const int r = tr + G * a;
+      lr[a] = (r > i && r < n) ? Ls[r + i * ld] : 0.f;
+    }
+#pragma unroll
+    for (int b = 0; b < R8; b++) {
+      const int c = tc + G * b;
+      yc[b] = (c <= i) ? vec[c] : 0.f;
+    }
+#pragma unroll
+    for (int a = 0; a < R8; a++)
+#pragma unroll
+      for (int b = 0; b < R8; b++) R[a][b] -= lr[a] * yc[b];
     __syncthreads();
   }
-  for (int c = threadIdx.x; c < n; c += blockDim.x) Y[(n - 1) + c * ld] *= dprev;
-  __syncthreads();
-  for (int j = warp; j < n; j += nw)
-    for (int i = lane; i < n; i += 32) {
-      if (i >= j) A[i + (int64_t)j * lda] = S[i + j * ld];
-      X[i + (int64_t)j * ldx] = Y[i + j * ld];
+#pragma unroll
+  for (int a = 0; a < R8; a++)
+#pragma unroll
+    for (int b = 0; b < R8; b++) {
+      const int i = tr + G * a, c = tc + G * b;
+      if (i < n && c < n) X[i + (int64_t)c * ldx] = (i >= c) ? R[a][b] : 0.f;
     }
 }
 
@@ -414,7 +676,7 @@ int grid1(int64_t work) { return (int)std::min<int64_t>((work + 255) / 256, 152 
 void top_rec(float* A, int64_t lda, float* X, int64_t ldx, int n, float* W, DevError* err,
              int level, cudaStream_t st) {
   if (n <= kLeaf) {
-    const size_t smem = 2 * (size_t)(kLeaf + 1) * kLeaf * sizeof(float);
+    const size_t smem = ((size_t)(kLeaf + 1) * kLeaf + kLeaf) * sizeof(float);
     static bool attr_set = false;
     if (!attr_set) {
       cudaFuncSetAttribute(chol_inv_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -460,6 +722,37 @@ void tc_gemm(int mode, int M, int N, int K, const float* A, int64_t rsa, int64_t
     launch_gemm<1>(M, N, K, A, rsa, csa, B, rsb, csb, C, ldc, alpha, beta, lower, err, st);
   else
     launch_gemm<2>(M, N, K, A, rsa, csa, B, rsb, csb, C, ldc, alpha, beta, lower, err, st);
+}
+
+template <int MODE>
+void launch_schur(const SchurTask* tasks, int ntask, int maxnw, const float* fac, float* arena,
+                  const Seg* segs, const int64_t* base, const int* ldn, const int* rank,
+                  DevError* err, cudaStream_t st) {
+  const size_t smem = 2 * TcMode<MODE>::kStageBytes + 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(schur_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr_set = true;
+  }
+  for (int t0 = 0; t0 < ntask; t0 += 65535) {
+    dim3 grid((maxnw + TN - 1) / TN, (maxnw + TM - 1) / TM, std::min(65535, ntask - t0));
+    count_launch();
+    schur_tc_kernel<MODE><<<grid, kTcThreads, smem, st>>>(tasks + t0, fac, arena, segs, base, ldn,
+                                                          rank, err);
+  }
+}
+
+void schur_tc(int mode, const SchurTask* tasks, int ntask, int maxnw, const float* fac,
+              float* arena, const Seg* segs, const int64_t* base, const int* ldn, const int* rank,
+              DevError* err, cudaStream_t st) {
+  if (ntask <= 0 || maxnw <= 0) return;
+  if (mode == 0)
+    launch_schur<0>(tasks, ntask, maxnw, fac, arena, segs, base, ldn, rank, err, st);
+  else if (mode == 1)
+    launch_schur<1>(tasks, ntask, maxnw, fac, arena, segs, base, ldn, rank, err, st);
+  else
+    launch_schur<2>(tasks, ntask, maxnw, fac, arena, segs, base, ldn, rank, err, st);
 }
 
 size_t dense_top_tc_scratch(int n) { return (size_t)(n / 2 + kLeaf) * (size_t)(n / 2 + kLeaf); }

@@ -20,7 +20,7 @@ OK = 0
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_SINGULAR",
           -5: "ERR_NOT_SPD", -6: "ERR_NO_CONVERGENCE", -7: "ERR_BUDGET", -8: "ERR_TIMEOUT",
           -9: "ERR_STATE"}
-PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
+PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3, "mixed_3xtf32": 4}
 KRYLOV = {"pcg": 0, "gmres": 1}
 
 

@@ -273,8 +273,8 @@ def test_cluster_qr_equals_single_cta(hs, precision):
 def test_dense_top_blocked(hs, precision):
     # a top level of more than 256 unknowns goes to the blocked multi-CTA
     # Cholesky and inverse factor (Alg. 1, dense factor when small enough);
-    # sizes not multiples of the 64-wide panels; mixed_tf32 takes the
-    # recursive tensor-core (3xTF32) top with 128-wide leaves
+    # sizes not multiples of the 64-wide panels (float64); the float32 modes
+    # take the recursive tensor-core (3xTF32) top with 128-wide leaves
     p = I.poisson((16, 16, 16))
     fac = _oracle(p, 64, 1e-2, top_size=2000)
     assert any(lv.top is not None and lv.top["n"] > 256 for lv in fac.levels)
@@ -331,4 +331,40 @@ def test_equilibrate_matches_oracle(hs, mk, leaf, eps, sym):
     x = x.cpu().numpy()
     for c in range(2):
         assert np.linalg.norm(b[c] - A @ x[c]) <= 1e-10 * np.linalg.norm(b[c]) * 1.0001
+    s.close()
+
+
+# Tensor-core precisions: the Schur-complement products run on tcgen05 with
+# TF32, 3xTF32 or BF16 operands (float32 accumulation) and the dense top on
+# 3xTF32 products.  Bars: the float64 Krylov solve still reaches 1e-10 (the
+# outer iteration recovers the accuracy, Sec. 5) in at most twice the
+# float64 iterations plus two, and M^{-1} b stays within the operand
+# rounding's reach of the oracle: 3xTF32 as float32 (2e-3), TF32 (10-bit
+# mantissa) 3e-2, BF16 (7-bit) 3e-1 -- all far below the O(1) differences a
+# wrong rank, block or sign would cause.
+TC_BOUND = {"mixed_3xtf32": 2e-3, "mixed_tf32": 3e-2, "mixed_bf16": 3e-1}
+
+
+@pytest.mark.parametrize("precision", ["mixed_tf32", "mixed_3xtf32", "mixed_bf16"])
+@pytest.mark.parametrize("name,mk,leaf,eps,top", [
+    ("poisson3d_16", lambda: I.poisson((16, 16, 16)), 64, 1e-2, 600),
+    ("poisson2d_64", lambda: I.poisson((64, 64)), 64, 1e-3, 0),
+])
+def test_tensor_core_precisions(hs, precision, name, mk, leaf, eps, top):
+    p = mk()
+    fac = _oracle(p, leaf, eps, top_size=top)
+    s = hs.Solver.from_problem(p, leaf_size=leaf, symmetric=1, top_size=top)
+    s.factor(eps, "fp64")
+    b = I.rhs(p.n, 2, seed=1005)
+    _, info64 = s.solve(torch.from_numpy(b).cuda(), krylov="pcg", tol=1e-10)
+    s.factor(eps, precision)
+    ref = H.solve(fac, b.T).T
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out, ref) < TC_BOUND[precision], _rel(out, ref)
+    x, info = s.solve(torch.from_numpy(b).cuda(), krylov="pcg", tol=1e-10)
+    A = p.scipy()
+    x = x.cpu().numpy()
+    for c in range(2):
+        assert np.linalg.norm(b[c] - A @ x[c]) <= 1.0001e-10 * np.linalg.norm(b[c])
+    assert info.iterations <= 2 * info64.iterations + 2, (info.iterations, info64.iterations)
     s.close()
