@@ -231,6 +231,84 @@ hsolve_status hsolve_tc_gemm(int mode, int M, int N, int K, const float* A,
                              int64_t rsb, int64_t csb, float* C, int64_t ldc,
                              float alpha, float beta, int lower, void* stream);
 
+/* ---- Serving runtime (a request loop over the solver; the paper has no
+ * counterpart: it is the service form of factoring once and solving many
+ * right-hand sides).  Worker threads take the oldest queued request whose
+ * matrix is idle, batch every queued request of that matrix behind it (up to
+ * max_batch_rhs columns), make the matrix's factorization resident if needed
+ * (analysis + factorization on the matrix's own CUDA stream, evicting least
+ * recently used idle factorizations while the resident bytes would exceed
+ * memory_budget) and solve the batch with one hsolve_solve call (one
+ * host-to-device copy of the batch, one copy back).
+ * Requests of different matrices run on different workers at once. */
+typedef struct hsolve_server hsolve_server;
+
+typedef struct {
+  int64_t memory_budget;  /* device bytes resident factorizations may hold
+                             (factors + largest level's blocks); a request
+                             whose matrix does not fit waits until busy ones
+                             finish (it runs alone if nothing else is
+                             resident); 0 = no limit; default 60 GiB */
+  int32_t max_batch_rhs;  /* most right-hand sides per batched solve (one
+                             request is never split); default 256 */
+  int32_t workers;        /* concurrent batches (threads); default 4 */
+} hsolve_server_opts;
+
+typedef struct {
+  int32_t status;         /* hsolve_status of the request's batch */
+  int32_t iterations;     /* Krylov iterations of the batch */
+  double rel_residual;    /* max relative residual over the batch */
+  double queue_ms;        /* submit -> batch start */
+  double service_ms;      /* batch start -> done (factorization included) */
+  double latency_ms;      /* submit -> done */
+  int32_t batch_rhs;      /* right-hand sides solved together */
+  int32_t factored;       /* 1: the batch factored the matrix first */
+} hsolve_server_result;
+
+typedef struct {
+  int64_t requests_submitted, requests_done, rhs_done, batches;
+  int64_t factorizations, evictions;
+  int64_t resident, resident_bytes, peak_resident_bytes, queued;
+} hsolve_server_stats;
+
+void hsolve_server_default_opts(hsolve_server_opts* opts);
+
+/* Start the workers (opts NULL = defaults).  Errors: HSOLVE_ERR_ARG. */
+hsolve_status hsolve_server_create(const hsolve_server_opts* opts,
+                                   hsolve_server** out);
+
+/* Register a matrix (host CSR and coordinates are copied; no device work
+ * until its first request) with the solver settings every request of it
+ * uses.  *matrix_id receives its id. */
+hsolve_status hsolve_server_add_matrix(hsolve_server* s, const hsolve_csr* A,
+                                       const double* coords, int dim,
+                                       const hsolve_opts* opts, double eps,
+                                       hsolve_precision prec,
+                                       hsolve_krylov krylov, double tol,
+                                       int maxit, int32_t* matrix_id);
+
+/* Queue a request: nrhs HOST right-hand sides, column-major with leading
+ * dimension ld >= n (copied).  Returns at once with *request_id. */
+hsolve_status hsolve_server_submit(hsolve_server* s, int32_t matrix_id,
+                                   const double* b, int32_t nrhs, int64_t ld,
+                                   int64_t* request_id);
+
+/* Wait up to timeout_s seconds for a request; on completion copy its
+ * solution to x (HOST, leading dimension ld; may be NULL), its record to res
+ * (may be NULL), forget the request and return its status.  Errors:
+ * HSOLVE_ERR_TIMEOUT (still pending; wait again), HSOLVE_ERR_ARG (unknown
+ * id). */
+hsolve_status hsolve_server_wait(hsolve_server* s, int64_t request_id,
+                                 double* x, int64_t ld,
+                                 hsolve_server_result* res, double timeout_s);
+
+hsolve_status hsolve_server_get_stats(hsolve_server* s,
+                                      hsolve_server_stats* out);
+
+/* Stop the workers (queued requests are dropped; running batches finish)
+ * and release every factorization. */
+void hsolve_server_destroy(hsolve_server* s);
+
 /* Statistics of the analysis and the last factorization. */
 hsolve_status hsolve_get_stats(const hsolve_handle* h, hsolve_stats* out);
 

@@ -23,7 +23,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
 
 SOURCES = ["analyze.cpp", "hsolve.cu", "kernels_dense.cu", "kernels_misc.cu", "kernels_apply.cu",
-           "kernels_qr.cu", "kernels_top.cu", "kernels_tc.cu"]
+           "kernels_qr.cu", "kernels_top.cu", "kernels_tc.cu", "server.cpp"]
 
 
 def _nvcc() -> str:

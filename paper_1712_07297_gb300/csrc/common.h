@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
 #include <cstddef>
 #include <string>
 #include <vector>
@@ -14,6 +15,10 @@ namespace hs {
 
 // Kernels launched by this process through the library (all handles).
 int64_t launches_total();
+// One process-wide lock around device (de)allocation and CUDA-graph capture:
+// an allocation's implicit synchronisation in one thread would invalidate a
+// capture running in another.
+std::mutex& device_mutex();
 void count_launch(int n = 1);
 
 // ---------------------------------------------------------------------------

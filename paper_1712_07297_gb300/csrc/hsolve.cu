@@ -73,14 +73,21 @@ struct DevBuf {
   }
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      std::lock_guard<std::mutex> lk(device_mutex());
+      cudaFree(p);
+    }
     p = nullptr;
     bytes = 0;
   }
   void alloc(size_t b) {
     release();
     if (b == 0) b = 16;
-    cudaError_t e = cudaMalloc(&p, b);
+    cudaError_t e;
+    {
+      std::lock_guard<std::mutex> lk(device_mutex());
+      e = cudaMalloc(&p, b);
+    }
     if (e != cudaSuccess) {
       p = nullptr;
       cudaGetLastError();
@@ -112,14 +119,25 @@ struct PinnedBuf {
   void* p = nullptr;
   size_t bytes = 0;
   ~PinnedBuf() {
-    if (p) cudaFreeHost(p);
+    if (p) {
+      std::lock_guard<std::mutex> lk(device_mutex());
+      cudaFreeHost(p);
+    }
   }
   void ensure(size_t b) {
     if (b <= bytes) return;
-    if (p) cudaFreeHost(p);
+    if (p) {
+      std::lock_guard<std::mutex> lk(device_mutex());
+      cudaFreeHost(p);
+    }
     p = nullptr;
     bytes = 0;
-    if (cudaMallocHost(&p, b) != cudaSuccess) {
+    cudaError_t e;
+    {
+      std::lock_guard<std::mutex> lk(device_mutex());
+      e = cudaMallocHost(&p, b);
+    }
+    if (e != cudaSuccess) {
       cudaGetLastError();
       throw Fail(HSOLVE_ERR_OOM, "cudaMallocHost failed");
     }
@@ -1205,7 +1223,12 @@ void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int6
     for (auto& x : h->graphs)
       if (x.nrhs == nrhs) g = &x;
     if (!g) {
+      std::lock_guard<std::mutex> lk(device_mutex());
       if (!h->cap_stream) HS_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      if (h->graphs.size() >= 8) {  // keep the graphs of the 8 latest widths
+        cudaGraphExecDestroy(h->graphs.front().exec);
+        h->graphs.erase(h->graphs.begin());
+      }
       const int64_t l0 = launches_total();
       HS_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
       apply_levels<real>(h, nrhs, h->cap_stream);
@@ -1835,7 +1858,10 @@ hsolve_status hsolve_tc_gemm(int mode, int M, int N, int K, const float* A, int6
   cudaGetLastError();
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   DevError* err = nullptr;
-  if (cudaMalloc(&err, sizeof(DevError)) != cudaSuccess) return HSOLVE_ERR_OOM;
+  {
+    std::lock_guard<std::mutex> lk(device_mutex());
+    if (cudaMalloc(&err, sizeof(DevError)) != cudaSuccess) return HSOLVE_ERR_OOM;
+  }
   DevError e{};
   hsolve_status rc = HSOLVE_OK;
   if (cudaMemsetAsync(err, 0, sizeof(DevError), st) != cudaSuccess) rc = HSOLVE_ERR_CUDA;
@@ -1848,7 +1874,10 @@ hsolve_status hsolve_tc_gemm(int mode, int M, int N, int K, const float* A, int6
     else if (e.code != 0)
       rc = (hsolve_status)e.code;
   }
-  cudaFree(err);
+  {
+    std::lock_guard<std::mutex> lk(device_mutex());
+    cudaFree(err);
+  }
   return rc;
 }
 

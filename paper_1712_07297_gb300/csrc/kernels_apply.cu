@@ -10,7 +10,9 @@
 //   bwd_t    x_s = T_R'^T z_s (rows split over CTAs)
 // Clusters of one class touch disjoint slots (their neighbour sets are
 // disjoint, Sec. 3.2), so no atomics are needed.  z and the partial sums are
-// level-sized scratch vectors owned by the factorization.
+// level-sized scratch vectors owned by the factorization.  Every kernel takes
+// a group of up to 8 right-hand sides per CTA (grid z over the groups): each
+// operator element read serves the whole group.
 #include <algorithm>
 
 #include "common.h"
@@ -21,65 +23,102 @@ namespace {
 
 constexpr int kRows = 64;   // output rows per CTA in the T' products
 constexpr int kCols = 64;   // neighbour columns per CTA
+// right-hand sides per CTA (grid z runs over the groups); wider groups cost
+// more registers than the operator reads they save
+template <typename real>
+struct Rb {
+  static constexpr int value = 8;
+};
+
+// The right-hand-side group of this CTA: columns r0 .. r0 + nr, groups of
+// rb <= Rb columns (rb is smaller when Rb slot vectors would not fit in
+// shared memory).
+struct RhsGroup {
+  int r0, nr;
+  __device__ RhsGroup(int nrhs, int rb)
+      : r0(blockIdx.z * rb), nr(min(rb, nrhs - (int)blockIdx.z * rb)) {}
+};
 
 template <typename real>
 __global__ void __launch_bounds__(256)
 fwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
              const real* __restrict__ fac, const real* __restrict__ y, real* __restrict__ z,
-             int64_t ldy, int nrhs) {
+             int64_t ldy, int nrhs, int rb) {
   extern __shared__ unsigned char smem_raw[];
-  real* ys = reinterpret_cast<real*>(smem_raw);
-  __shared__ real red[256];
+  real* ys = reinterpret_cast<real*>(smem_raw);  // RB x m
+  constexpr int RB = Rb<real>::value;
+  __shared__ real red[RB][256];
   const ApplyRec rc = recs[ids[blockIdx.y]];
   const int m = rc.m;
   if (rc.k == m) return;
   const int i0 = blockIdx.x * kRows;
   if (i0 >= m) return;
+  const RhsGroup g(nrhs, rb);
   const real* T = fac + rc.T;
   const int ii = threadIdx.x % kRows, part = threadIdx.x / kRows;  // 4 parts over l
   const int i = i0 + ii;
-  for (int r = 0; r < nrhs; r++) {
-    const real* yr = y + rc.voff + (int64_t)r * ldy;
-    for (int l = threadIdx.x; l < m; l += blockDim.x) ys[l] = yr[l];
-    __syncthreads();
-    real acc = 0;
-    if (i < m)
-      for (int l = part; l < m; l += 4) acc += T[i + (int64_t)l * m] * ys[l];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (part == 0 && i < m)
-      z[rc.voff + i + (int64_t)r * ldy] = red[ii] + red[ii + 64] + red[ii + 128] + red[ii + 192];
-    __syncthreads();
-  }
+  for (int r = 0; r < g.nr; r++)
+    for (int l = threadIdx.x; l < m; l += blockDim.x)
+      ys[r * m + l] = y[rc.voff + l + (int64_t)(g.r0 + r) * ldy];
+  __syncthreads();
+  real acc[RB];
+#pragma unroll
+  for (int r = 0; r < RB; r++) acc[r] = 0;
+  if (i < m)
+    for (int l = part; l < m; l += 4) {
+      const real t = T[i + (int64_t)l * m];
+#pragma unroll
+      for (int r = 0; r < RB; r++)
+        if (r < g.nr) acc[r] += t * ys[r * m + l];
+    }
+#pragma unroll
+  for (int r = 0; r < RB; r++) red[r][threadIdx.x] = acc[r];
+  __syncthreads();
+  if (part == 0 && i < m)
+    for (int r = 0; r < g.nr; r++)
+      z[rc.voff + i + (int64_t)(g.r0 + r) * ldy] =
+          red[r][ii] + red[r][ii + 64] + red[r][ii + 128] + red[r][ii + 192];
 }
 
 template <typename real>
 __global__ void __launch_bounds__(256)
 fwd_nbr_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
                const real* __restrict__ fac, const int64_t* __restrict__ vmap,
-               real* __restrict__ y, const real* __restrict__ z, int64_t ldy, int nrhs) {
+               real* __restrict__ y, const real* __restrict__ z, int64_t ldy, int nrhs, int rb) {
   const ApplyRec rc = recs[ids[blockIdx.y]];
   const int m = rc.m, k = rc.k, f = m - k;
   if (k == m) return;
+  const RhsGroup g(nrhs, rb);
+  constexpr int RB = Rb<real>::value;
   if (blockIdx.x == 0)
-    for (int r = 0; r < nrhs; r++)
+    for (int r = 0; r < g.nr; r++)
       for (int i = threadIdx.x; i < m; i += blockDim.x)
-        y[rc.voff + i + (int64_t)r * ldy] = z[rc.voff + i + (int64_t)r * ldy];
+        y[rc.voff + i + (int64_t)(g.r0 + r) * ldy] = z[rc.voff + i + (int64_t)(g.r0 + r) * ldy];
   const int c0 = blockIdx.x * kCols;
   if (c0 >= rc.nw) return;
   const int c1 = min(rc.nw, c0 + kCols);
   const real* BL = fac + (rc.sym ? rc.Y : rc.XT) + k;  // column c: B_L[c, :]
   const int64_t* vm = vmap + rc.map;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int r = 0; r < nrhs; r++) {
-    const real* zf = z + rc.voff + k + (int64_t)r * ldy;
-    for (int c = c0 + warp; c < c1; c += nwarp) {
-      const real* col = BL + (int64_t)c * m;
-      real acc = 0;
-      for (int i = lane; i < f; i += 32) acc += col[i] * zf[i];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) y[vm[c] + (int64_t)r * ldy] -= acc;
+  const real* zf = z + rc.voff + k + (int64_t)g.r0 * ldy;
+  for (int c = c0 + warp; c < c1; c += nwarp) {
+    const real* col = BL + (int64_t)c * m;
+    real acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; r++) acc[r] = 0;
+    for (int i = lane; i < f; i += 32) {
+      const real b = col[i];
+#pragma unroll
+      for (int r = 0; r < RB; r++)
+        if (r < g.nr) acc[r] += b * zf[i + (int64_t)r * ldy];
     }
+#pragma unroll
+    for (int r = 0; r < RB; r++)
+      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < RB; r++)
+        if (r < g.nr) y[vm[c] + (int64_t)(g.r0 + r) * ldy] -= acc[r];
   }
 }
 
@@ -87,27 +126,36 @@ template <typename real>
 __global__ void __launch_bounds__(256)
 bwd_part_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
                 const real* __restrict__ fac, const int64_t* __restrict__ vmap,
-                const real* __restrict__ y, real* __restrict__ part, int64_t ldy, int nrhs) {
-  __shared__ real xn[kCols];
+                const real* __restrict__ y, real* __restrict__ part, int64_t ldy, int nrhs, int rb) {
+  constexpr int RB = Rb<real>::value;
+  __shared__ real xn[RB][kCols];
   const ApplyRec rc = recs[ids[blockIdx.y]];
   const int m = rc.m, k = rc.k, f = m - k;
   if (k == m) return;
   const int c0 = blockIdx.x * kCols;
   if (c0 >= rc.nw) return;
+  const RhsGroup g(nrhs, rb);
   const int nc = min(rc.nw, c0 + kCols) - c0;
   const int nchunk = (rc.nw + kCols - 1) / kCols;
   const real* BR = fac + rc.Y + k;
   const int64_t* vm = vmap + rc.map;
   real* pr = part + rc.part * nrhs;
-  for (int r = 0; r < nrhs; r++) {
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) xn[c] = y[vm[c0 + c] + (int64_t)r * ldy];
-    __syncthreads();
-    for (int i = threadIdx.x; i < f; i += blockDim.x) {
-      real acc = 0;
-      for (int c = 0; c < nc; c++) acc += BR[i + (int64_t)(c0 + c) * m] * xn[c];
-      pr[((int64_t)r * nchunk + blockIdx.x) * f + i] = acc;
+  for (int r = 0; r < g.nr; r++)
+    for (int c = threadIdx.x; c < nc; c += blockDim.x)
+      xn[r][c] = y[vm[c0 + c] + (int64_t)(g.r0 + r) * ldy];
+  __syncthreads();
+  for (int i = threadIdx.x; i < f; i += blockDim.x) {
+    real acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; r++) acc[r] = 0;
+    for (int c = 0; c < nc; c++) {
+      const real b = BR[i + (int64_t)(c0 + c) * m];
+#pragma unroll
+      for (int r = 0; r < RB; r++) acc[r] += b * xn[r][c];
     }
-    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RB; r++)
+      if (r < g.nr) pr[((int64_t)(g.r0 + r) * nchunk + blockIdx.x) * f + i] = acc[r];
   }
 }
 
@@ -115,13 +163,14 @@ template <typename real>
 __global__ void __launch_bounds__(256)
 bwd_z_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
              const real* __restrict__ y, real* __restrict__ z, const real* __restrict__ part,
-             int64_t ldy, int nrhs) {
+             int64_t ldy, int nrhs, int rb) {
   const ApplyRec rc = recs[ids[blockIdx.x]];
   const int m = rc.m, k = rc.k, f = m - k;
   if (k == m) return;
+  const RhsGroup g(nrhs, rb);
   const int nchunk = (rc.nw + kCols - 1) / kCols;
   const real* pr = part + rc.part * nrhs;
-  for (int r = 0; r < nrhs; r++) {
+  for (int r = g.r0; r < g.r0 + g.nr; r++) {
     const real* ys = y + rc.voff + (int64_t)r * ldy;
     real* zs = z + rc.voff + (int64_t)r * ldy;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -137,35 +186,58 @@ template <typename real>
 __global__ void __launch_bounds__(256)
 bwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
              const real* __restrict__ fac, real* __restrict__ y, const real* __restrict__ z,
-             int64_t ldy, int nrhs) {
+             int64_t ldy, int nrhs, int rb) {
   extern __shared__ unsigned char smem_raw[];
-  real* zsm = reinterpret_cast<real*>(smem_raw);
+  real* zsm = reinterpret_cast<real*>(smem_raw);  // RB x m
   const ApplyRec rc = recs[ids[blockIdx.y]];
   const int m = rc.m;
   if (rc.k == m) return;
   const int i0 = blockIdx.x * kRows;
   if (i0 >= m) return;
+  const RhsGroup g(nrhs, rb);
+  constexpr int RB = Rb<real>::value;
   const int i1 = min(m, i0 + kRows);
   const real* TRt = fac + (rc.sym ? rc.T : rc.TR);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int r = 0; r < nrhs; r++) {
-    const real* zs = z + rc.voff + (int64_t)r * ldy;
-    for (int l = threadIdx.x; l < m; l += blockDim.x) zsm[l] = zs[l];
-    __syncthreads();
-    for (int i = i0 + warp; i < i1; i += nwarp) {
-      const real* col = TRt + (int64_t)i * m;
-      real acc = 0;
-      for (int l = lane; l < m; l += 32) acc += col[l] * zsm[l];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) y[rc.voff + i + (int64_t)r * ldy] = acc;
+  for (int r = 0; r < g.nr; r++)
+    for (int l = threadIdx.x; l < m; l += blockDim.x)
+      zsm[r * m + l] = z[rc.voff + l + (int64_t)(g.r0 + r) * ldy];
+  __syncthreads();
+  for (int i = i0 + warp; i < i1; i += nwarp) {
+    const real* col = TRt + (int64_t)i * m;
+    real acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; r++) acc[r] = 0;
+    for (int l = lane; l < m; l += 32) {
+      const real t = col[l];
+#pragma unroll
+      for (int r = 0; r < RB; r++)
+        if (r < g.nr) acc[r] += t * zsm[r * m + l];
     }
-    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RB; r++)
+      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < RB; r++)
+        if (r < g.nr) y[rc.voff + i + (int64_t)(g.r0 + r) * ldy] = acc[r];
   }
 }
 
+// Right-hand sides per CTA: Rb, fewer when Rb slot vectors of maxm entries
+// would exceed 160 KB of shared memory (the dense top's long vectors).
+template <typename real>
+int group_size(int maxm) {
+  const size_t per = sizeof(real) * (size_t)std::max(maxm, 1);
+  return (int)std::max<size_t>(1, std::min<size_t>(Rb<real>::value, (160u * 1024u) / per));
+}
+
+// The dynamic shared-memory limit of a kernel: static arrays (up to 32 KB
+// here) plus the dynamic part may pass 48 KB even when the dynamic part alone
+// does not, so the limit is always raised to the launch's request.
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024)
+  if (bytes > 0)
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -176,14 +248,16 @@ void Launch<real>::apply_fwd(const ApplyRec* recs, const int* ids, int nids, int
                              const real* fac, const int64_t* vmap, real* y, real* z, int64_t ldy,
                              int nrhs, cudaStream_t st) {
   if (nids <= 0) return;
-  const size_t sm = sizeof(real) * (size_t)std::max(maxm, 1);
+  const int rb = group_size<real>(maxm);
+  const int nz = (nrhs + rb - 1) / rb;
+  const size_t sm = sizeof(real) * (size_t)rb * std::max(maxm, 1);
   set_smem(fwd_t_kernel<real>, sm);
-  dim3 g1((maxm + kRows - 1) / kRows, nids);
+  dim3 g1((maxm + kRows - 1) / kRows, nids, nz);
   count_launch();
-  fwd_t_kernel<real><<<g1, 256, sm, st>>>(recs, ids, fac, y, z, ldy, nrhs);
-  dim3 g2(std::max(1, (maxnw + kCols - 1) / kCols), nids);
+  fwd_t_kernel<real><<<g1, 256, sm, st>>>(recs, ids, fac, y, z, ldy, nrhs, rb);
+  dim3 g2(std::max(1, (maxnw + kCols - 1) / kCols), nids, nz);
   count_launch();
-  fwd_nbr_kernel<real><<<g2, 256, 0, st>>>(recs, ids, fac, vmap, y, z, ldy, nrhs);
+  fwd_nbr_kernel<real><<<g2, 256, 0, st>>>(recs, ids, fac, vmap, y, z, ldy, nrhs, rb);
 }
 
 template <typename real>
@@ -191,18 +265,20 @@ void Launch<real>::apply_bwd(const ApplyRec* recs, const int* ids, int nids, int
                              const real* fac, const int64_t* vmap, real* y, real* z, real* part,
                              int64_t ldy, int nrhs, cudaStream_t st) {
   if (nids <= 0) return;
+  const int rb = group_size<real>(maxm);
+  const int nz = (nrhs + rb - 1) / rb;
   if (maxnw > 0) {
-    dim3 g1((maxnw + kCols - 1) / kCols, nids);
+    dim3 g1((maxnw + kCols - 1) / kCols, nids, nz);
     count_launch();
-    bwd_part_kernel<real><<<g1, 256, 0, st>>>(recs, ids, fac, vmap, y, part, ldy, nrhs);
+    bwd_part_kernel<real><<<g1, 256, 0, st>>>(recs, ids, fac, vmap, y, part, ldy, nrhs, rb);
   }
   count_launch();
-  bwd_z_kernel<real><<<nids, 256, 0, st>>>(recs, ids, y, z, part, ldy, nrhs);
-  const size_t sm = sizeof(real) * (size_t)std::max(maxm, 1);
+  bwd_z_kernel<real><<<dim3(nids, 1, nz), 256, 0, st>>>(recs, ids, y, z, part, ldy, nrhs, rb);
+  const size_t sm = sizeof(real) * (size_t)rb * std::max(maxm, 1);
   set_smem(bwd_t_kernel<real>, sm);
-  dim3 g3((maxm + kRows - 1) / kRows, nids);
+  dim3 g3((maxm + kRows - 1) / kRows, nids, nz);
   count_launch();
-  bwd_t_kernel<real><<<g3, 256, sm, st>>>(recs, ids, fac, y, z, ldy, nrhs);
+  bwd_t_kernel<real><<<g3, 256, sm, st>>>(recs, ids, fac, y, z, ldy, nrhs, rb);
 }
 
 template struct Launch<double>;

@@ -21,6 +21,10 @@ namespace hs {
 
 static std::atomic<int64_t> g_launches{0};
 int64_t launches_total() { return g_launches.load(); }
+std::mutex& device_mutex() {
+  static std::mutex m;
+  return m;
+}
 void count_launch(int n) { g_launches += n; }
 
 namespace {

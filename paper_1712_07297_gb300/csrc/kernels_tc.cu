@@ -657,12 +657,12 @@ void launch_gemm(int M, int N, int K, const float* A, int64_t rsa, int64_t csa, 
                  bool lower, DevError* err, cudaStream_t st) {
   if (M <= 0 || N <= 0) return;
   const size_t smem = 2 * TcMode<MODE>::kStageBytes + 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static const bool attr_set = [smem] {
     cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   dim3 grid((M + TM - 1) / TM, (N + TN - 1) / TN);
   count_launch();
   tc_gemm_kernel<MODE><<<grid, kTcThreads, smem, st>>>(M, N, K, A, rsa, csa, B, rsb, csb, C, ldc,
@@ -677,12 +677,12 @@ void top_rec(float* A, int64_t lda, float* X, int64_t ldx, int n, float* W, DevE
              int level, cudaStream_t st) {
   if (n <= kLeaf) {
     const size_t smem = ((size_t)(kLeaf + 1) * kLeaf + kLeaf) * sizeof(float);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static const bool attr_set = [smem] {
       cudaFuncSetAttribute(chol_inv_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
-      attr_set = true;
-    }
+      return true;
+    }();
+    (void)attr_set;
     count_launch();
     chol_inv_leaf_kernel<<<1, 256, smem, st>>>(A, lda, X, ldx, n, err, level);
     return;
@@ -729,12 +729,12 @@ void launch_schur(const SchurTask* tasks, int ntask, int maxnw, const float* fac
                   const Seg* segs, const int64_t* base, const int* ldn, const int* rank,
                   DevError* err, cudaStream_t st) {
   const size_t smem = 2 * TcMode<MODE>::kStageBytes + 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static const bool attr_set = [smem] {
     cudaFuncSetAttribute(schur_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   for (int t0 = 0; t0 < ntask; t0 += 65535) {
     dim3 grid((maxnw + TN - 1) / TN, (maxnw + TM - 1) / TM, std::min(65535, ntask - t0));
     count_launch();

@@ -89,6 +89,38 @@ EXPORTS = {
 
 TC_MODES = {"tf32": 0, "3xtf32": 1, "bf16": 2}
 
+
+class ServerOpts(C.Structure):
+    _fields_ = [("memory_budget", C.c_int64), ("max_batch_rhs", C.c_int32),
+                ("workers", C.c_int32)]
+
+
+class ServerResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("rel_residual", C.c_double),
+                ("queue_ms", C.c_double), ("service_ms", C.c_double),
+                ("latency_ms", C.c_double), ("batch_rhs", C.c_int32), ("factored", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in (
+        "requests_submitted", "requests_done", "rhs_done", "batches", "factorizations",
+        "evictions", "resident", "resident_bytes", "peak_resident_bytes", "queued")]
+
+
+EXPORTS.update({
+    "hsolve_server_default_opts": (None, [C.POINTER(ServerOpts)]),
+    "hsolve_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
+    "hsolve_server_add_matrix": (C.c_int, [C.c_void_p, C.POINTER(Csr), C.c_void_p, C.c_int,
+                                           C.POINTER(Opts), C.c_double, C.c_int, C.c_int,
+                                           C.c_double, C.c_int, C.POINTER(C.c_int32)]),
+    "hsolve_server_submit": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int64,
+                                       C.POINTER(C.c_int64)]),
+    "hsolve_server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                     C.POINTER(ServerResult), C.c_double]),
+    "hsolve_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "hsolve_server_destroy": (None, [C.c_void_p]),
+})
+
 _lib = None
 
 
@@ -293,3 +325,72 @@ def tc_gemm(mode, A, B, C_, alpha=1.0, beta=0.0, lower=False, stream=None):
                                  B.data_ptr(), B.stride(0), B.stride(1), C_.data_ptr(),
                                  max(C_.stride(1), M), float(alpha), float(beta), int(lower), st))
     return C_
+
+
+class Server:
+    """The serving runtime (hsolve_server_*): register matrices, submit
+    host right-hand sides (numpy (nrhs, n)), wait for solutions."""
+
+    def __init__(self, memory_budget=60 << 30, max_batch_rhs=256, workers=4):
+        o = ServerOpts(int(memory_budget), int(max_batch_rhs), int(workers))
+        self.h = C.c_void_p()
+        _check(load().hsolve_server_create(C.byref(o), C.byref(self.h)))
+        self.n = {}
+
+    def add_matrix(self, prob, eps, precision="mixed_fp32", krylov="pcg", tol=1e-10, maxit=500,
+                   leaf_size=128, symmetric=-1, top_size=0, equilibrate=0):
+        import numpy as np
+        rp = np.ascontiguousarray(prob.rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(prob.col, dtype=np.int32)
+        val = np.ascontiguousarray(prob.val, dtype=np.float64)
+        xyz = np.ascontiguousarray(prob.coords, dtype=np.float64)
+        csr = Csr(prob.n, len(col), rp.ctypes.data, col.ctypes.data, val.ctypes.data)
+        o = default_opts()
+        o.leaf_size, o.symmetric, o.top_size, o.equilibrate = leaf_size, symmetric, top_size, \
+            equilibrate
+        mid = C.c_int32()
+        p = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        _check(load().hsolve_server_add_matrix(self.h, C.byref(csr), xyz.ctypes.data,
+                                               xyz.shape[1], C.byref(o), float(eps), p,
+                                               KRYLOV[krylov], float(tol), int(maxit),
+                                               C.byref(mid)))
+        self.n[mid.value] = prob.n
+        return mid.value
+
+    def submit(self, matrix_id, b):
+        import numpy as np
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        if b.ndim == 1:
+            b = b[None, :]
+        rid = C.c_int64()
+        _check(load().hsolve_server_submit(self.h, int(matrix_id), b.ctypes.data, b.shape[0],
+                                           b.shape[1], C.byref(rid)))
+        return rid.value, b.shape
+
+    def wait(self, ticket, timeout=600.0, want_x=True):
+        """Block until the request is served; returns (x (nrhs, n) or None,
+        result record)."""
+        import numpy as np
+        rid, shape = ticket
+        x = np.empty(shape, dtype=np.float64) if want_x else None
+        res = ServerResult()
+        code = load().hsolve_server_wait(self.h, rid, x.ctypes.data if want_x else None,
+                                         shape[1], C.byref(res), float(timeout))
+        _check(code)
+        return x, {k: getattr(res, k) for k, _ in ServerResult._fields_}
+
+    def stats(self):
+        st = ServerStats()
+        _check(load().hsolve_server_get_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().hsolve_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -223,3 +223,31 @@ def workload(name: str):
         "poisson3d_128": (lambda: poisson((128, 128, 128)), dict(leaf=128, eps=1e-2, nrhs=8, krylov="gmres", rhs_seed=1003)),
     }[name]
     return w[0](), dict(w[1])
+
+
+# The serving stream: six matrix families (2D Poisson 32^2, 128^2, 512^2; 3D
+# Poisson 16^3, 64^3; 3D high-contrast diffusion 32^3, factored as S A S
+# with the diagonal equilibration: its 1e4 coefficient contrast otherwise
+# costs definiteness at this eps), eps 1e-2, mixed precision.  Families are drawn uniformly, 1-32 right-hand sides each,
+# exponential inter-arrival times (Poisson arrivals).
+SERVING_FAMILIES = {
+    "poisson2d_32": (lambda: poisson((32, 32)), dict(leaf=64)),
+    "poisson2d_128": (lambda: poisson((128, 128)), dict(leaf=64)),
+    "poisson2d_512": (lambda: poisson((512, 512)), dict(leaf=64)),
+    "poisson3d_16": (lambda: poisson((16, 16, 16)), dict(leaf=64)),
+    "poisson3d_64": (lambda: poisson((64, 64, 64)), dict(leaf=128)),
+    "hcdiff3d_32": (lambda: high_contrast((32, 32, 32), seed=5), dict(leaf=128, equilibrate=1)),
+}
+
+
+def serving_stream(n_requests: int = 2000, rate: float = 200.0, seed: int = 3000,
+                   families=None, max_rhs: int = 32):
+    """Requests (arrival time s, family, nrhs, rhs seed) of a Poisson stream."""
+    fams = list(families or SERVING_FAMILIES)
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=n_requests)
+    t = np.cumsum(gaps) - gaps[0]
+    fam = rng.integers(0, len(fams), size=n_requests)
+    nrhs = rng.integers(1, max_rhs + 1, size=n_requests)
+    return [(float(t[i]), fams[int(fam[i])], int(nrhs[i]), seed * 10007 + i)
+            for i in range(n_requests)]
