@@ -23,15 +23,13 @@ namespace {
 
 constexpr int kRows = 64;   // output rows per CTA in the T' products
 constexpr int kCols = 64;   // neighbour columns per CTA
-// right-hand sides per CTA (grid z runs over the groups); wider groups cost
-// more registers than the operator reads they save
-template <typename real>
-struct Rb {
-  static constexpr int value = 8;
-};
+// right-hand sides per CTA (grid z runs over the groups): 8 when there are
+// several, 1 for a single one (a wider group's predicated-off products would
+// still be issued, which the float64 pipe cannot afford)
+constexpr int kRbWide = 8;
 
 // The right-hand-side group of this CTA: columns r0 .. r0 + nr, groups of
-// rb <= Rb columns (rb is smaller when Rb slot vectors would not fit in
+// rb <= RB columns (rb is smaller when RB slot vectors would not fit in
 // shared memory).
 struct RhsGroup {
   int r0, nr;
@@ -39,14 +37,13 @@ struct RhsGroup {
       : r0(blockIdx.z * rb), nr(min(rb, nrhs - (int)blockIdx.z * rb)) {}
 };
 
-template <typename real>
+template <typename real, int RB>
 __global__ void __launch_bounds__(256)
 fwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
              const real* __restrict__ fac, const real* __restrict__ y, real* __restrict__ z,
              int64_t ldy, int nrhs, int rb) {
   extern __shared__ unsigned char smem_raw[];
   real* ys = reinterpret_cast<real*>(smem_raw);  // RB x m
-  constexpr int RB = Rb<real>::value;
   __shared__ real red[RB][256];
   const ApplyRec rc = recs[ids[blockIdx.y]];
   const int m = rc.m;
@@ -80,7 +77,7 @@ fwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
           red[r][ii] + red[r][ii + 64] + red[r][ii + 128] + red[r][ii + 192];
 }
 
-template <typename real>
+template <typename real, int RB>
 __global__ void __launch_bounds__(256)
 fwd_nbr_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
                const real* __restrict__ fac, const int64_t* __restrict__ vmap,
@@ -89,7 +86,6 @@ fwd_nbr_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
   const int m = rc.m, k = rc.k, f = m - k;
   if (k == m) return;
   const RhsGroup g(nrhs, rb);
-  constexpr int RB = Rb<real>::value;
   if (blockIdx.x == 0)
     for (int r = 0; r < g.nr; r++)
       for (int i = threadIdx.x; i < m; i += blockDim.x)
@@ -122,12 +118,11 @@ fwd_nbr_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
   }
 }
 
-template <typename real>
+template <typename real, int RB>
 __global__ void __launch_bounds__(256)
 bwd_part_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
                 const real* __restrict__ fac, const int64_t* __restrict__ vmap,
                 const real* __restrict__ y, real* __restrict__ part, int64_t ldy, int nrhs, int rb) {
-  constexpr int RB = Rb<real>::value;
   __shared__ real xn[RB][kCols];
   const ApplyRec rc = recs[ids[blockIdx.y]];
   const int m = rc.m, k = rc.k, f = m - k;
@@ -159,7 +154,7 @@ bwd_part_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
   }
 }
 
-template <typename real>
+template <typename real, int RB>
 __global__ void __launch_bounds__(256)
 bwd_z_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
              const real* __restrict__ y, real* __restrict__ z, const real* __restrict__ part,
@@ -182,7 +177,7 @@ bwd_z_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
   }
 }
 
-template <typename real>
+template <typename real, int RB>
 __global__ void __launch_bounds__(256)
 bwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
              const real* __restrict__ fac, real* __restrict__ y, const real* __restrict__ z,
@@ -195,7 +190,6 @@ bwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
   const int i0 = blockIdx.x * kRows;
   if (i0 >= m) return;
   const RhsGroup g(nrhs, rb);
-  constexpr int RB = Rb<real>::value;
   const int i1 = min(m, i0 + kRows);
   const real* TRt = fac + (rc.sym ? rc.T : rc.TR);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -224,12 +218,13 @@ bwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
   }
 }
 
-// Right-hand sides per CTA: Rb, fewer when Rb slot vectors of maxm entries
-// would exceed 160 KB of shared memory (the dense top's long vectors).
+// Right-hand sides per CTA: rbmax, fewer when rbmax slot vectors of maxm
+// entries would exceed 160 KB of shared memory (the dense top's long
+// vectors).
 template <typename real>
-int group_size(int maxm) {
+int group_size(int maxm, int rbmax) {
   const size_t per = sizeof(real) * (size_t)std::max(maxm, 1);
-  return (int)std::max<size_t>(1, std::min<size_t>(Rb<real>::value, (160u * 1024u) / per));
+  return (int)std::max<size_t>(1, std::min<size_t>(rbmax, (160u * 1024u) / per));
 }
 
 // The dynamic shared-memory limit of a kernel: static arrays (up to 32 KB
@@ -241,6 +236,43 @@ void set_smem(K kernel, size_t bytes) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <typename real, int RB>
+void launch_fwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int maxnw,
+                const real* fac, const int64_t* vmap, real* y, real* z, int64_t ldy, int nrhs,
+                cudaStream_t st) {
+  const int rb = group_size<real>(maxm, RB);
+  const int nz = (nrhs + rb - 1) / rb;
+  const size_t sm = sizeof(real) * (size_t)rb * std::max(maxm, 1);
+  set_smem(fwd_t_kernel<real, RB>, sm);
+  dim3 g1((maxm + kRows - 1) / kRows, nids, nz);
+  count_launch();
+  fwd_t_kernel<real, RB><<<g1, 256, sm, st>>>(recs, ids, fac, y, z, ldy, nrhs, rb);
+  dim3 g2(std::max(1, (maxnw + kCols - 1) / kCols), nids, nz);
+  count_launch();
+  fwd_nbr_kernel<real, RB><<<g2, 256, 0, st>>>(recs, ids, fac, vmap, y, z, ldy, nrhs, rb);
+}
+
+template <typename real, int RB>
+void launch_bwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int maxnw,
+                const real* fac, const int64_t* vmap, real* y, real* z, real* part, int64_t ldy,
+                int nrhs, cudaStream_t st) {
+  const int rb = group_size<real>(maxm, RB);
+  const int nz = (nrhs + rb - 1) / rb;
+  if (maxnw > 0) {
+    dim3 g1((maxnw + kCols - 1) / kCols, nids, nz);
+    count_launch();
+    bwd_part_kernel<real, RB><<<g1, 256, 0, st>>>(recs, ids, fac, vmap, y, part, ldy, nrhs, rb);
+  }
+  count_launch();
+  bwd_z_kernel<real, RB><<<dim3(nids, 1, nz), 256, 0, st>>>(recs, ids, y, z, part, ldy, nrhs,
+                                                             rb);
+  const size_t sm = sizeof(real) * (size_t)rb * std::max(maxm, 1);
+  set_smem(bwd_t_kernel<real, RB>, sm);
+  dim3 g3((maxm + kRows - 1) / kRows, nids, nz);
+  count_launch();
+  bwd_t_kernel<real, RB><<<g3, 256, sm, st>>>(recs, ids, fac, y, z, ldy, nrhs, rb);
+}
+
 }  // namespace
 
 template <typename real>
@@ -248,16 +280,10 @@ void Launch<real>::apply_fwd(const ApplyRec* recs, const int* ids, int nids, int
                              const real* fac, const int64_t* vmap, real* y, real* z, int64_t ldy,
                              int nrhs, cudaStream_t st) {
   if (nids <= 0) return;
-  const int rb = group_size<real>(maxm);
-  const int nz = (nrhs + rb - 1) / rb;
-  const size_t sm = sizeof(real) * (size_t)rb * std::max(maxm, 1);
-  set_smem(fwd_t_kernel<real>, sm);
-  dim3 g1((maxm + kRows - 1) / kRows, nids, nz);
-  count_launch();
-  fwd_t_kernel<real><<<g1, 256, sm, st>>>(recs, ids, fac, y, z, ldy, nrhs, rb);
-  dim3 g2(std::max(1, (maxnw + kCols - 1) / kCols), nids, nz);
-  count_launch();
-  fwd_nbr_kernel<real><<<g2, 256, 0, st>>>(recs, ids, fac, vmap, y, z, ldy, nrhs, rb);
+  if (nrhs == 1)
+    launch_fwd<real, 1>(recs, ids, nids, maxm, maxnw, fac, vmap, y, z, ldy, nrhs, st);
+  else
+    launch_fwd<real, kRbWide>(recs, ids, nids, maxm, maxnw, fac, vmap, y, z, ldy, nrhs, st);
 }
 
 template <typename real>
@@ -265,20 +291,11 @@ void Launch<real>::apply_bwd(const ApplyRec* recs, const int* ids, int nids, int
                              const real* fac, const int64_t* vmap, real* y, real* z, real* part,
                              int64_t ldy, int nrhs, cudaStream_t st) {
   if (nids <= 0) return;
-  const int rb = group_size<real>(maxm);
-  const int nz = (nrhs + rb - 1) / rb;
-  if (maxnw > 0) {
-    dim3 g1((maxnw + kCols - 1) / kCols, nids, nz);
-    count_launch();
-    bwd_part_kernel<real><<<g1, 256, 0, st>>>(recs, ids, fac, vmap, y, part, ldy, nrhs, rb);
-  }
-  count_launch();
-  bwd_z_kernel<real><<<dim3(nids, 1, nz), 256, 0, st>>>(recs, ids, y, z, part, ldy, nrhs, rb);
-  const size_t sm = sizeof(real) * (size_t)rb * std::max(maxm, 1);
-  set_smem(bwd_t_kernel<real>, sm);
-  dim3 g3((maxm + kRows - 1) / kRows, nids, nz);
-  count_launch();
-  bwd_t_kernel<real><<<g3, 256, sm, st>>>(recs, ids, fac, y, z, ldy, nrhs, rb);
+  if (nrhs == 1)
+    launch_bwd<real, 1>(recs, ids, nids, maxm, maxnw, fac, vmap, y, z, part, ldy, nrhs, st);
+  else
+    launch_bwd<real, kRbWide>(recs, ids, nids, maxm, maxnw, fac, vmap, y, z, part, ldy, nrhs,
+                              st);
 }
 
 template struct Launch<double>;
