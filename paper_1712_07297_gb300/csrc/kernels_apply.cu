@@ -227,13 +227,18 @@ int group_size(int maxm, int rbmax) {
   return (int)std::max<size_t>(1, std::min<size_t>(rbmax, (160u * 1024u) / per));
 }
 
-// The dynamic shared-memory limit of a kernel: static arrays (up to 32 KB
-// here) plus the dynamic part may pass 48 KB even when the dynamic part alone
-// does not, so the limit is always raised to the launch's request.
-template <typename K>
-void set_smem(K kernel, size_t bytes) {
-  if (bytes > 0)
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// The dynamic shared-memory limit of a kernel is raised once, to a ceiling
+// above every request (at most 160 KB of slot vectors) plus its static arrays,
+// and never lowered: a CUDA graph captured earlier may hold a launch of the
+// same kernel with a larger request than the current one.
+constexpr int kSmemCeiling = 192 * 1024;
+template <auto Kernel>
+void set_smem() {
+  static const bool once = [] {
+    cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCeiling);
+    return true;
+  }();
+  (void)once;
 }
 
 template <typename real, int RB>
@@ -243,7 +248,7 @@ void launch_fwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int ma
   const int rb = group_size<real>(maxm, RB);
   const int nz = (nrhs + rb - 1) / rb;
   const size_t sm = sizeof(real) * (size_t)rb * std::max(maxm, 1);
-  set_smem(fwd_t_kernel<real, RB>, sm);
+  set_smem<fwd_t_kernel<real, RB>>();
   dim3 g1((maxm + kRows - 1) / kRows, nids, nz);
   count_launch();
   fwd_t_kernel<real, RB><<<g1, 256, sm, st>>>(recs, ids, fac, y, z, ldy, nrhs, rb);
@@ -267,7 +272,7 @@ void launch_bwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int ma
   bwd_z_kernel<real, RB><<<dim3(nids, 1, nz), 256, 0, st>>>(recs, ids, y, z, part, ldy, nrhs,
                                                              rb);
   const size_t sm = sizeof(real) * (size_t)rb * std::max(maxm, 1);
-  set_smem(bwd_t_kernel<real, RB>, sm);
+  set_smem<bwd_t_kernel<real, RB>>();
   dim3 g3((maxm + kRows - 1) / kRows, nids, nz);
   count_launch();
   bwd_t_kernel<real, RB><<<g3, 256, sm, st>>>(recs, ids, fac, y, z, ldy, nrhs, rb);
