@@ -108,6 +108,21 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
+def _traffic(kernel, nclu, launches):
+    """DRAM bytes per launch of the dominant kernel from its committed ncu
+    summary (measured on a smaller case and scaled by the clusters a launch
+    processes here), or None when no summary gives a per-cluster figure."""
+    import glob
+    import re
+    if kernel != "prep" or not launches:
+        return None
+    for f in glob.glob(os.path.join(ROOT, "profiles", "prep_kernel*.md")):
+        m = re.search(r"traffic_bytes_per_cluster:\s*(\d+)", open(f).read())
+        if m:
+            return int(m.group(1)) * nclu / launches
+    return None
+
+
 def _pct(xs, q):
     xs = sorted(xs)
     if not xs:
@@ -203,6 +218,12 @@ def run_gpu(args, rank, world):
     # the substitution sweeps alone (Alg. 2): HBM-bound, one graph launch each
     s.factor(eps, args.mixed)
     stm = s.stats()
+    # clusters the per-cluster kernels processed (levels below the dense top)
+    nclu_done = 0
+    for lv in range(stm["levels"]):
+        sizes, _, _ = s.level(lv)
+        if len(sizes) > 1:
+            nclu_done += int((np.asarray(sizes) > 0).sum())
     u = torch.empty_like(b)
     for _ in range(3):
         s.apply(b, u)
@@ -234,7 +255,8 @@ def run_gpu(args, rank, world):
     ach = fl / (ms_dom * 1e-3) / 1e12
     peak = alu_peak_tflops("f32", sm_mhz)
     roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": None, "launches_per_step": nl_dom,
+            "frac": ach / peak, "traffic": _traffic(dom, nclu_done, nl_dom),
+            "launches_per_step": nl_dom,
             "ms_per_step": ms_dom,
             "work": "algorithmic float32 flops per step (library counters)",
             "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x median SM clock"}
