@@ -8,6 +8,8 @@
 //   bwd_part partial sums of B_R x_N over column chunks (deterministic order)
 //   bwd_z    z_s = [x_c; x_f - sum of partials]
 //   bwd_t    x_s = T_R'^T z_s (rows split over CTAs)
+//   (classes of clusters of at most 256 unknowns: bwd_zt does bwd_z and
+//   bwd_t on one CTA per cluster)
 // Clusters of one class touch disjoint slots (their neighbour sets are
 // disjoint, Sec. 3.2), so no atomics are needed.  z and the partial sums are
 // level-sized scratch vectors owned by the factorization.  Every kernel takes
@@ -218,6 +220,59 @@ bwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
   }
 }
 
+// Backward step of a cluster on one CTA (clusters of at most kZtMax
+// unknowns): z = [x_c; x_f - sum of the partials of B_R x_N] in shared
+// memory, then x_s = T_R'^T z written over the cluster's slots.  The CTA
+// reads every slot of its cluster before any is written, so no separate z
+// pass is needed.
+constexpr int kZtMax = 256;
+
+template <typename real, int RB>
+__global__ void __launch_bounds__(256)
+bwd_zt_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
+              const real* __restrict__ fac, real* __restrict__ y, const real* __restrict__ part,
+              int64_t ldy, int nrhs, int rb) {
+  extern __shared__ unsigned char smem_raw[];
+  real* zsm = reinterpret_cast<real*>(smem_raw);  // rb x m
+  const ApplyRec rc = recs[ids[blockIdx.y]];
+  const int m = rc.m, k = rc.k, f = m - k;
+  if (k == m) return;
+  const RhsGroup g(nrhs, rb);
+  const int nchunk = (rc.nw + kCols - 1) / kCols;
+  const real* pr = part + rc.part * nrhs;
+  for (int r = 0; r < g.nr; r++) {
+    const int rr = g.r0 + r;
+    for (int l = threadIdx.x; l < m; l += blockDim.x) {
+      real v = y[rc.voff + l + (int64_t)rr * ldy];
+      if (l >= k)
+        for (int q = 0; q < nchunk; q++) v -= pr[((int64_t)rr * nchunk + q) * f + (l - k)];
+      zsm[r * m + l] = v;
+    }
+  }
+  __syncthreads();
+  const real* TRt = fac + (rc.sym ? rc.T : rc.TR);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int i = warp; i < m; i += nwarp) {
+    const real* col = TRt + (int64_t)i * m;
+    real acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; r++) acc[r] = 0;
+    for (int l = lane; l < m; l += 32) {
+      const real t = col[l];
+#pragma unroll
+      for (int r = 0; r < RB; r++)
+        if (r < g.nr) acc[r] += t * zsm[r * m + l];
+    }
+#pragma unroll
+    for (int r = 0; r < RB; r++)
+      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < RB; r++)
+        if (r < g.nr) y[rc.voff + i + (int64_t)(g.r0 + r) * ldy] = acc[r];
+  }
+}
+
 // Right-hand sides per CTA: rbmax, fewer when rbmax slot vectors of maxm
 // entries would exceed 160 KB of shared memory (the dense top's long
 // vectors).
@@ -267,6 +322,14 @@ void launch_bwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int ma
     dim3 g1((maxnw + kCols - 1) / kCols, nids, nz);
     count_launch();
     bwd_part_kernel<real, RB><<<g1, 256, 0, st>>>(recs, ids, fac, vmap, y, part, ldy, nrhs, rb);
+  }
+  if (maxm <= kZtMax) {
+    const size_t sm = sizeof(real) * (size_t)rb * std::max(maxm, 1);
+    set_smem<bwd_zt_kernel<real, RB>>();
+    count_launch();
+    bwd_zt_kernel<real, RB><<<dim3(1, nids, nz), 256, sm, st>>>(recs, ids, fac, y, part, ldy,
+                                                                nrhs, rb);
+    return;
   }
   count_launch();
   bwd_z_kernel<real, RB><<<dim3(nids, 1, nz), 256, 0, st>>>(recs, ids, y, z, part, ldy, nrhs,

@@ -256,16 +256,39 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
     for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
       if (nrm[t] < 0.0) continue;
       real* col = Gs + (int64_t)t * ldsm;
-      real w = 0;
-      for (int i = j; i < m; i++) w += vloc[i] * col[i];
-      w *= tj;
-      real s = 0;
-      for (int i = j; i < m; i++) {
-        const real v = col[i] - w * vloc[i];
-        col[i] = v;
-        if (i > j) s += v * v;
+      // four independent partial sums (combined in a fixed order) keep four
+      // products in flight instead of one dependent chain
+      real w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+      int i = j;
+      for (; i + 3 < m; i += 4) {
+        w0 += vloc[i] * col[i];
+        w1 += vloc[i + 1] * col[i + 1];
+        w2 += vloc[i + 2] * col[i + 2];
+        w3 += vloc[i + 3] * col[i + 3];
       }
-      nrm[t] = (double)s;
+      for (; i < m; i++) w0 += vloc[i] * col[i];
+      const real w = ((w0 + w1) + (w2 + w3)) * tj;
+      col[j] -= w * vloc[j];
+      real s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      i = j + 1;
+      for (; i + 3 < m; i += 4) {
+        const real a0 = col[i] - w * vloc[i], a1 = col[i + 1] - w * vloc[i + 1];
+        const real a2 = col[i + 2] - w * vloc[i + 2], a3 = col[i + 3] - w * vloc[i + 3];
+        col[i] = a0;
+        col[i + 1] = a1;
+        col[i + 2] = a2;
+        col[i + 3] = a3;
+        s0 += a0 * a0;
+        s1 += a1 * a1;
+        s2 += a2 * a2;
+        s3 += a3 * a3;
+      }
+      for (; i < m; i++) {
+        const real a = col[i] - w * vloc[i];
+        col[i] = a;
+        s0 += a * a;
+      }
+      nrm[t] = (double)((s0 + s1) + (s2 + s3));
     }
     __syncthreads();
     k = j + 1;
