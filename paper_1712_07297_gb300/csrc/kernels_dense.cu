@@ -22,7 +22,12 @@ namespace hs {
 
 namespace {
 
-constexpr int kPrepThreads = 256;
+// threads of the per-cluster kernel: 512 in float32 (more warps share each
+// barrier-separated step), 256 in float64 (register budget)
+template <typename real>
+struct PrepThreads {
+  static constexpr int value = sizeof(real) == 4 ? 512 : 256;
+};
 constexpr double kPivotTieRtol = 1e-10;
 constexpr int GT = 64, GK = 16;  // CTA GEMM tile and inner chunk
 
@@ -33,20 +38,23 @@ __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 template <>
 __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 
-// C (M x N, ldc) = alpha * op(A) * op(B) + beta * C, whole CTA (256 threads,
-// 64 x 64 output tiles, 4 x 4 outputs per thread, inner chunks of 16 staged
-// in shared memory `sh` of 2 * 16 * 65 reals).  C must not alias A or B.
+// C (M x N, ldc) = alpha * op(A) * op(B) + beta * C, whole CTA (NT =
+// PrepThreads threads, 64 x 64 output tiles, GR x 4 outputs per thread with
+// GR = 1024 / NT, inner chunks of 16 staged in shared memory `sh` of
+// 2 * 16 * 65 reals).  C must not alias A or B.
 template <typename real>
 __device__ void cta_gemm(int M, int N, int K, const real* A, int lda, bool ta, const real* B,
                          int ldb, bool tb, real* C, int ldc, real alpha, real beta, real* sh) {
+  constexpr int NT = PrepThreads<real>::value;
+  constexpr int GR = 1024 / NT, RS = NT / 16;  // rows per thread, row stride
   real* As = sh;
   real* Bs = sh + GK * (GT + 1);
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   for (int i0 = 0; i0 < M; i0 += GT)
     for (int j0 = 0; j0 < N; j0 += GT) {
-      real acc[4][4];
+      real acc[GR][4];
 #pragma unroll
-      for (int p = 0; p < 4; p++)
+      for (int p = 0; p < GR; p++)
 #pragma unroll
         for (int q = 0; q < 4; q++) acc[p][q] = 0;
       for (int l0 = 0; l0 < K; l0 += GK) {
@@ -81,24 +89,23 @@ __device__ void cta_gemm(int M, int N, int K, const real* A, int lda, bool ta, c
         __syncthreads();
 #pragma unroll
         for (int l = 0; l < GK; l++) {
-          real a[4], b[4];
+          real a[GR], b[4];
 #pragma unroll
-          for (int p = 0; p < 4; p++) {
-            a[p] = As[l * (GT + 1) + ty + 16 * p];
-            b[p] = Bs[l * (GT + 1) + tx + 16 * p];
-          }
+          for (int p = 0; p < GR; p++) a[p] = As[l * (GT + 1) + ty + RS * p];
 #pragma unroll
-          for (int p = 0; p < 4; p++)
+          for (int q = 0; q < 4; q++) b[q] = Bs[l * (GT + 1) + tx + 16 * q];
+#pragma unroll
+          for (int p = 0; p < GR; p++)
 #pragma unroll
             for (int q = 0; q < 4; q++) acc[p][q] += a[p] * b[q];
         }
         __syncthreads();
       }
 #pragma unroll
-      for (int p = 0; p < 4; p++)
+      for (int p = 0; p < GR; p++)
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-          int gi = i0 + ty + 16 * p, gj = j0 + tx + 16 * q;
+          int gi = i0 + ty + RS * p, gj = j0 + tx + 16 * q;
           if (gi < M && gj < N) {
             real c = alpha * acc[p][q];
             if (beta != real(0)) c += beta * C[gi + (int64_t)gj * ldc];
@@ -629,14 +636,14 @@ __device__ void report(DevError* err, int code, int s, int level, int* rank, int
 }
 
 template <typename real>
-__global__ void __launch_bounds__(kPrepThreads)
+__global__ void __launch_bounds__(PrepThreads<real>::value)
 prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* __restrict__ fac,
             real* __restrict__ ws_all, double* __restrict__ wsd_all,
             const Seg* __restrict__ segs, int* rank,
             double eps, double noise_rtol, int sym, int max_rank, int smem_mats, int smem_m,
             DevError* err, int level, long long* dbg) {
-  __shared__ double red_d[kPrepThreads];
-  __shared__ int red_i[kPrepThreads + 1];
+  __shared__ double red_d[PrepThreads<real>::value];
+  __shared__ int red_i[PrepThreads<real>::value + 1];
   __shared__ int sflag;
   __shared__ int s_ncol;
   __shared__ double s_amax;
@@ -947,7 +954,7 @@ void Launch<real>::prep(const PrepTask* tasks_dev, int ntask, real* arena, real*
   cudaFuncSetAttribute(prep_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)std::max<size_t>(smem, 48 * 1024));
   count_launch();
-  prep_kernel<real><<<ntask, kPrepThreads, smem, st>>>(tasks_dev, arena, fac, ws, wsd, segs,
+  prep_kernel<real><<<ntask, PrepThreads<real>::value, smem, st>>>(tasks_dev, arena, fac, ws, wsd, segs,
                                                         rank, eps, noise_rtol, sym, max_rank, mats,
                                                         maxm, err, level, dbg);
 }
