@@ -33,6 +33,7 @@ namespace hs {
 namespace {
 
 constexpr double kTieRtol = 1e-10;
+constexpr int kQrThreads = 256;  // threads per CTA of the cluster QR (more only add barrier cost)
 constexpr int kMaxGrid = 1 << 20;
 
 // Dynamic shared memory of one CTA: every array starts on a 16-byte boundary
@@ -45,7 +46,7 @@ struct QrSmem {
     nrm = G + al((size_t)ldsm * cc * sz);
     oidx = nrm + al((size_t)cc * sizeof(double));
     tpos = oidx + al((size_t)cc * sizeof(int));
-    vloc = tpos + al((size_t)256 * sizeof(int));
+    vloc = tpos + al((size_t)kQrThreads * sizeof(int));
     total = vloc + al((size_t)ldsm * sz);
   }
 };
@@ -83,7 +84,7 @@ __device__ double block_max(double v, double* red) {
 }
 
 template <typename real>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kQrThreads)
 qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ arena,
                   real* __restrict__ ws_all, double* __restrict__ wsd_all,
                   const Seg* __restrict__ segs, int* rank, const int* __restrict__ cnt,
@@ -93,7 +94,7 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
   const int cr = (int)cl.block_rank();
   const PrepTask tk = tasks[blockIdx.x / CL];
   const int m = tk.m, c = tk.ncolG;
-  __shared__ double red_d[256];
+  __shared__ double red_d[kQrThreads];
   __shared__ Exchange xch;
   extern __shared__ __align__(16) unsigned char dsm[];
   const QrSmem lay(ldsm, ccmax, (int)sizeof(real));
@@ -172,7 +173,7 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
   const int steps = min(m, c);
   double r11 = 0;
   int k = 0;
-  __shared__ unsigned long long red_u[8];
+  __shared__ unsigned long long red_u[kQrThreads / 32];
   __shared__ double s_M, s_r;
   __shared__ int s_owner;
   for (int j = 0; j < steps; j++) {
@@ -384,7 +385,7 @@ void Launch<real>::qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, in
     const int nt = std::min(4096, ntask - t0);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nt * CL);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(kQrThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
