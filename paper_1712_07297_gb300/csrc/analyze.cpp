@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <queue>
 
 #include "common.h"
 
@@ -118,11 +119,34 @@ void build_level_pattern(LevelPattern& L, const std::vector<std::vector<int>>& a
       o += int64_t(L.ld[i]) * std::max(L.m[L.col[p]], 1);
     }
   L.arena_elems = std::max<int64_t>(o, 1);
-  // greedy distance-2 colouring in index order
+  // greedy distance-2 colouring in smallest-last order: remove the cluster
+  // with the fewest remaining distance-<=2 neighbours (ties: lowest index)
+  // until none is left; colour in reverse removal order, each cluster taking
+  // the smallest colour unused by its coloured distance-<=2 neighbours
+  std::vector<int> deg(nc), order;
+  order.reserve(nc);
+  for (int i = 0; i < nc; i++) deg[i] = L.ptr[i + 1] - L.ptr[i] - 1;  // row minus self
+  std::priority_queue<std::pair<int, int>, std::vector<std::pair<int, int>>,
+                      std::greater<std::pair<int, int>>>
+      heap;
+  for (int i = 0; i < nc; i++) heap.emplace(deg[i], i);
+  std::vector<char> removed(nc, 0);
+  while (!heap.empty()) {
+    const auto [d, i] = heap.top();
+    heap.pop();
+    if (removed[i] || d != deg[i]) continue;  // a stale entry
+    removed[i] = 1;
+    order.push_back(i);
+    for (int p = L.ptr[i]; p < L.ptr[i + 1]; p++) {
+      const int j = L.col[p];
+      if (j != i && !removed[j]) heap.emplace(--deg[j], j);
+    }
+  }
+  std::reverse(order.begin(), order.end());
   L.colour.assign(nc, -1);
   int ncol = 0;
   std::vector<int> used(1, -1);
-  for (int i = 0; i < nc; i++) {
+  for (int i : order) {
     for (int p = L.ptr[i]; p < L.ptr[i + 1]; p++) {
       int j = L.col[p];
       if (j != i && L.colour[j] >= 0) {
