@@ -263,6 +263,7 @@ typedef struct {
   double latency_ms;      /* submit -> done */
   int32_t batch_rhs;      /* right-hand sides solved together */
   int32_t factored;       /* 1: the batch factored the matrix first */
+  char message[128];      /* the library's error text when status != OK */
 } hsolve_server_result;
 
 typedef struct {

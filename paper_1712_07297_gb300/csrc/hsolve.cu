@@ -494,6 +494,11 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   int* rank = d_rank.as<int>();
   std::vector<ApplyRec> recs(nc);
   std::vector<int64_t> vmap;
+  {
+    int64_t wsum = 0;
+    for (int s = 0; s < nc; s++) wsum += wmax[s];
+    vmap.reserve((size_t)wsum);  // one slot per neighbour unknown, at most
+  }
   std::vector<int> fillcols(nc, 0), fillw(nc, 0), nzcols(nc, -1);
   FL.cls.clear();
   // rank-independent part of every cluster's tasks, built in parallel: its
@@ -566,6 +571,8 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     h->factor_flops += 2.0 / 3.0 * nf * nf * nf;
     h->apply_bytes += (int64_t)sizeof(real) * 2 * ((int64_t)n * n + 2 * (int64_t)n);
   }
+  struct Nb { int j, w; int64_t p_sj, p_js; int ia; };
+  std::vector<Nb> nbN, nbW;
   for (size_t c = 0; c < P.classes.size() && !dense_top; c++) {
     std::unique_ptr<HostTimer> hb(new HostTimer(h, "host.build"));
     std::vector<int> S;
@@ -589,8 +596,10 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       const int s = S[t];
       const int m = cur[s];
       maxm = std::max(maxm, m);
-      struct Nb { int j, w; int64_t p_sj, p_js; int ia; };
-      std::vector<Nb> N, W;
+      std::vector<Nb>& N = nbN;  // reused across clusters (capacity kept)
+      std::vector<Nb>& W = nbW;
+      N.clear();
+      W.clear();
       int nn_all = 0;  // neighbours in the pattern (index base of pre_sb)
       for (auto& e0 : pre_nb[s]) {
         const int ia = e0.kind == 1 ? nn_all++ : -1;

@@ -951,8 +951,14 @@ void Launch<real>::prep(const PrepTask* tasks_dev, int ntask, real* arena, real*
   else if (2 * one + vec <= budget) mats = 2;
   else if (one + vec <= budget) mats = 1;
   const size_t smem = mats * one + vec;
-  cudaFuncSetAttribute(prep_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)std::max<size_t>(smem, 48 * 1024));
+  // the limit is raised once to the budget and never lowered: host threads
+  // factoring different matrices launch this kernel concurrently
+  static const bool limit_set = [budget] {
+    cudaFuncSetAttribute(prep_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)budget);
+    return true;
+  }();
+  (void)limit_set;
   count_launch();
   prep_kernel<real><<<ntask, PrepThreads<real>::value, smem, st>>>(tasks_dev, arena, fac, ws, wsd, segs,
                                                         rank, eps, noise_rtol, sym, max_rank, mats,

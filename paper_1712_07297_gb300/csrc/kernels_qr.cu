@@ -33,6 +33,7 @@ namespace hs {
 namespace {
 
 constexpr double kTieRtol = 1e-10;
+constexpr size_t kQrSmemCap = 200 * 1024;  // dynamic shared memory per CTA, at most
 constexpr int kQrThreads = 256;  // threads per CTA of the cluster QR (more only add barrier cost)
 constexpr int kMaxGrid = 1 << 20;
 
@@ -357,7 +358,7 @@ void Launch<real>::count_nz(const PrepTask* tasks_dev, int ntask, int maxc, cons
 template <typename real>
 int Launch<real>::qr_cluster_size(int maxm, int maxc) {
   for (int CL = 1; CL <= 16; CL *= 2) {
-    if (qr_cluster_smem(maxm, maxc, CL) <= 200 * 1024) return CL;
+    if (qr_cluster_smem(maxm, maxc, CL) <= kQrSmemCap) return CL;
   }
   return 0;
 }
@@ -377,10 +378,17 @@ void Launch<real>::qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, in
   const double noise_rtol = sizeof(real) == 8 ? 1e-14 : 1e-6;
   const size_t smem = qr_cluster_smem(maxm, maxc, CL);
   const int cc = (maxc + CL - 1) / CL;
-  cudaFuncSetAttribute(qr_cluster_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)std::max<size_t>(smem, 48 * 1024));
-  if (CL > 8)
+  // the limit is raised once to the sizing cap (qr_cluster_size keeps every
+  // launch at or below it) and never lowered: host threads factoring
+  // different matrices launch this kernel concurrently
+  static const bool limit_set = [] {
+    cudaFuncSetAttribute(qr_cluster_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kQrSmemCap);
+    // clusters of 16 CTAs (the largest qr_cluster_size picks) are non-portable
     cudaFuncSetAttribute(qr_cluster_kernel<real>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return true;
+  }();
+  (void)limit_set;
   for (int t0 = 0; t0 < ntask; t0 += 4096) {
     const int nt = std::min(4096, ntask - t0);
     cudaLaunchConfig_t cfg = {};

@@ -20,7 +20,9 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <deque>
 #include <map>
 #include <memory>
@@ -227,11 +229,22 @@ void hsolve_server::worker() {
     }
     hsolve_stats hs{};
     if (M.h) hsolve_get_stats(M.h, &hs);
+    std::string msg;
+    if (st != HSOLVE_OK && M.h) msg = hsolve_last_error(M.h);
 
     lk.lock();
     const auto t_done = Clock::now();
+    // a failed batch (other than a plain non-convergence) leaves no handle
+    // behind: the matrix's next batch analyses and factors it again
+    const bool keep = M.h && (st == HSOLVE_OK || st == HSOLVE_ERR_NO_CONVERGENCE);
+    if (!factored && !keep && M.h) {
+      hsolve_destroy(M.h);
+      M.h = nullptr;
+      resident_bytes -= M.bytes;
+      M.bytes = 0;
+    }
     if (factored) {
-      if (M.h && st != HSOLVE_ERR_NOT_SPD && st != HSOLVE_ERR_SINGULAR) {
+      if (keep) {
         // charge the measured size: factors plus the largest level's blocks
         const int64_t real_bytes = hs.factor_bytes + hs.block_bytes;
         resident_bytes += real_bytes - M.bytes;
@@ -254,6 +267,7 @@ void hsolve_server::worker() {
       c0 += r->nrhs;
       r->t_done = t_done;
       r->res.status = (int32_t)st;
+      std::snprintf(r->res.message, sizeof(r->res.message), "%s", msg.c_str());
       r->res.iterations = info.iterations;
       r->res.rel_residual = info.rel_residual;
       r->res.queue_ms = ms_between(r->t_submit, r->t_start);

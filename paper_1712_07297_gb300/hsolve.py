@@ -98,7 +98,8 @@ class ServerOpts(C.Structure):
 class ServerResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("rel_residual", C.c_double),
                 ("queue_ms", C.c_double), ("service_ms", C.c_double),
-                ("latency_ms", C.c_double), ("batch_rhs", C.c_int32), ("factored", C.c_int32)]
+                ("latency_ms", C.c_double), ("batch_rhs", C.c_int32), ("factored", C.c_int32),
+                ("message", C.c_char * 128)]
 
 
 class ServerStats(C.Structure):
@@ -376,7 +377,8 @@ class Server:
         res = ServerResult()
         code = load().hsolve_server_wait(self.h, rid, x.ctypes.data if want_x else None,
                                          shape[1], C.byref(res), float(timeout))
-        _check(code)
+        if code != OK:
+            raise HsolveError(code, res.message.decode(errors="replace"))
         return x, {k: getattr(res, k) for k, _ in ServerResult._fields_}
 
     def stats(self):
