@@ -347,11 +347,12 @@ hsolve_status hsolve_server_submit(hsolve_server* s, int32_t matrix_id, const do
                                    int32_t nrhs, int64_t ld, int64_t* request_id) {
   if (!s || !b || !request_id || nrhs < 1) return HSOLVE_ERR_ARG;
   std::unique_ptr<Request> r(new Request());
+  int64_t n = 0;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (matrix_id < 0 || matrix_id >= (int32_t)s->mats.size()) return HSOLVE_ERR_ARG;
+    n = s->mats[matrix_id]->n;
   }
-  const int64_t n = s->mats[matrix_id]->n;
   if (ld < n) return HSOLVE_ERR_ARG;
   r->matrix = matrix_id;
   r->nrhs = nrhs;
