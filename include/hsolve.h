@@ -158,6 +158,20 @@ hsolve_status hsolve_analyze(const hsolve_csr* A, const double* coords, int dim,
  * then holds no factorization), HSOLVE_ERR_OOM, HSOLVE_ERR_CUDA. */
 hsolve_status hsolve_factor(hsolve_handle* h, double eps, hsolve_precision prec);
 
+/* Test entry point: hsolve_factor with the rank of every cluster fixed in
+ * advance (Eq. lra keeps exactly that many pivoted-QR directions, fewer only
+ * where the fill block has no more nonzero ones; neither eps nor the
+ * rounding-noise floor plays a part), so that
+ * a float32 factorization can be compared with a float64 reference at
+ * identical ranks.  ranks: the per-cluster ranks of levels 0..nlevels-1
+ * concatenated (clusters in index order); counts[l]: clusters of level l,
+ * which must equal the level's cluster count (HSOLVE_ERR_ARG otherwise).
+ * Levels beyond nlevels (and the dense top) are factored as usual with
+ * eps = 0.  Host pointers; copied. */
+hsolve_status hsolve_factor_forced(hsolve_handle* h, hsolve_precision prec,
+                                   const int32_t* ranks, const int32_t* counts,
+                                   int32_t nlevels);
+
 /* Preconditioner application (Alg. 2): out = M^{-1} rhs where M is the
  * factorization.  rhs and out are DEVICE pointers, column-major n x nrhs with
  * leading dimension ld; they may alias.  Errors: HSOLVE_ERR_STATE before a

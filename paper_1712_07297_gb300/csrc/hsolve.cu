@@ -254,6 +254,9 @@ struct hsolve_handle {
     LevelPattern Q;
   };
   std::vector<PatCache> pcache;
+  // hsolve_factor_forced: per level, the rank of every cluster
+  bool force_ranks = false;
+  std::vector<std::vector<int>> forced;
   std::string err;
 };
 
@@ -487,7 +490,18 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   real* fac = FL.fac.as<real>();
   DevBuf d_rank;
   d_rank.alloc(sizeof(int) * std::max(nc, 1));
-  {
+  // forced ranks (hsolve_factor_forced): the kernels take rank[s] as the
+  // rank of cluster s (max_rank < 0 tells them so)
+  const bool forced = h->force_ranks && level < (int)h->forced.size();
+  if (forced && (int)h->forced[level].size() != nc)
+    throw Fail(HSOLVE_ERR_ARG, "forced ranks: level " + std::to_string(level) + " has " +
+                                   std::to_string(nc) + " clusters");
+  const int max_rank_arg = forced ? -1 : h->opts.max_rank;
+  if (forced) {
+    HS_CUDA(cudaMemcpyAsync(d_rank.p, h->forced[level].data(), sizeof(int) * nc,
+                            cudaMemcpyHostToDevice, h->st));
+    HS_CUDA(cudaStreamSynchronize(h->st));  // the host vector is pageable
+  } else {
     // clusters never processed (m = 0) report rank 0
     HS_CUDA(cudaMemsetAsync(d_rank.p, 0, sizeof(int) * std::max(nc, 1), h->st));
   }
@@ -834,7 +848,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         timed_lv(h, "qr_cluster", level, 1, [&] {
           Launch<real>::qr_cluster(d_qrt, (int)qrt.size(), qm, nzmax, CL, arena, ws,
                                    h->wsd.as<double>(), d_segs, rank, h->cnt.as<int>(), eps,
-                                   h->opts.max_rank, h->st);
+                                   max_rank_arg, h->st);
         });
       }
     }
@@ -852,7 +866,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     timed_lv(h, "prep", level, 1, [&] {
       Launch<real>::prep(d_prep, nt, arena, fac, ws,
                          h->wsd.as<double>(), d_segs, rank, eps, sym ? 1 : 0,
-                         h->opts.max_rank, maxm, h->d_err.as<DevError>(), level, dbg, h->st);
+                         max_rank_arg, maxm, h->d_err.as<DevError>(), level, dbg, h->st);
     });
     if (dbg) {
       // per checkpoint interval: the slowest cluster of the class, in ms at
@@ -1797,6 +1811,23 @@ hsolve_status hsolve_factor(hsolve_handle* h, double eps, hsolve_precision prec)
     return set_err(h, HSOLVE_ERR_OOM, "host allocation failed");
   }
   return HSOLVE_OK;
+}
+
+hsolve_status hsolve_factor_forced(hsolve_handle* h, hsolve_precision prec, const int32_t* ranks,
+                                   const int32_t* counts, int32_t nlevels) {
+  if (!h || !ranks || !counts || nlevels < 1) return HSOLVE_ERR_ARG;
+  h->forced.assign(nlevels, {});
+  int64_t o = 0;
+  for (int l = 0; l < nlevels; l++) {
+    if (counts[l] < 0) return HSOLVE_ERR_ARG;
+    h->forced[l].assign(ranks + o, ranks + o + counts[l]);
+    o += counts[l];
+  }
+  h->force_ranks = true;
+  const hsolve_status st = hsolve_factor(h, 0.0, prec);
+  h->force_ranks = false;
+  h->forced.clear();
+  return st;
 }
 
 hsolve_status hsolve_apply(hsolve_handle* h, const double* rhs, double* out, int nrhs, int64_t ld) {

@@ -28,7 +28,12 @@ template <typename real>
 struct PrepThreads {
   static constexpr int value = sizeof(real) == 4 ? 512 : 256;
 };
-constexpr double kPivotTieRtol = 1e-10;
+constexpr double kPivotTieRtol = 1e-10;  // LU pivot search
+// near-ties of the column-pivoted QR, relative: 1e-10 in float64; float32
+// squared norms carry ~1e-7 relative rounding, so ties of exact arithmetic
+// are recognised within 1e-5
+template <typename real>
+__device__ __forceinline__ double qr_tie_rtol() { return sizeof(real) == 8 ? 1e-10 : 1e-5; }
 constexpr int GT = 64, GK = 16;  // CTA GEMM tile and inner chunk
 
 template <typename real>
@@ -355,7 +360,7 @@ __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, 
       if (mx == 0.0) break;
       int best = INT_MAX;
       for (int t = j + threadIdx.x; t < c; t += blockDim.x)
-        if (nrm2[t] >= (1.0 - kPivotTieRtol) * mx) best = min(best, (int)orig[t]);
+        if (nrm2[t] >= (1.0 - qr_tie_rtol<real>()) * mx) best = min(best, (int)orig[t]);
       best = cta_min_i(best, red_i);
       for (int t = j + threadIdx.x; t < c; t += blockDim.x)
         if ((int)orig[t] == best) red_i[blockDim.x] = t;
@@ -777,6 +782,11 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
   int k = 0;
   int kmax = m;
   if (max_rank > 0) kmax = min(kmax, max_rank);
+  if (max_rank < 0) {  // forced rank (set by the host in rank[s]): no eps, no floor
+    kmax = min(kmax, rank[tk.s]);
+    eps = 0.0;
+    noise_rtol = 0.0;
+  }
   if (qr_done) {
     k = rank[tk.s];
   } else if (sketched) {

@@ -32,7 +32,11 @@ namespace hs {
 
 namespace {
 
-constexpr double kTieRtol = 1e-10;
+// near-ties of the pivot search, relative: 1e-10 in float64; in float32 the
+// squared norms carry ~1e-7 relative rounding, so ties of exact arithmetic
+// are recognised within 1e-5
+template <typename real>
+__device__ __forceinline__ double tie_rtol() { return sizeof(real) == 8 ? 1e-10 : 1e-5; }
 constexpr size_t kQrSmemCap = 200 * 1024;  // dynamic shared memory per CTA, at most
 constexpr int kQrThreads = 256;  // threads per CTA of the cluster QR (more only add barrier cost)
 constexpr int kMaxGrid = 1 << 20;
@@ -115,7 +119,8 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
   double amx = 0;
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x)
     amx = fmax(amx, fabs((double)arena[tk.a_ss + idx % m + (int64_t)(idx / m) * tk.ld]));
-  const double floor = noise_rtol * block_max(amx, red_d);
+  // forced ranks keep every direction up to the forced count (no floor)
+  const double floor = max_rank < 0 ? 0.0 : noise_rtol * block_max(amx, red_d);
 
   // The count pass flagged the nonzero gathered columns (flags[q] != 0) and
   // counted them (nz); CTA cr keeps nonzero columns cr*cz .. (cr+1)*cz - 1
@@ -170,7 +175,10 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
   }
   __syncthreads();
 
-  const int kmax = max_rank > 0 ? min(m, max_rank) : m;
+  // max_rank < 0: the rank of every cluster is forced to rank[s] (set by the
+  // host before the launch, read before any CTA of the cluster can write it)
+  const int kmax = max_rank > 0 ? min(m, max_rank) : (max_rank < 0 ? min(m, rank[tk.s]) : m);
+  if (max_rank < 0) eps = 0.0;
   const int steps = min(m, c);
   double r11 = 0;
   int k = 0;
@@ -202,7 +210,7 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
     //    (original index, local slot) per candidate, the smallest wins
     unsigned long long key = ~0ull;
     for (int t = threadIdx.x; t < nloc; t += blockDim.x)
-      if (nrm[t] >= (1.0 - kTieRtol) * M) {
+      if (nrm[t] >= (1.0 - tie_rtol<real>()) * M) {
         const unsigned long long kk = ((unsigned long long)oidx[t] << 32) | (unsigned)t;
         key = kk < key ? kk : key;
       }

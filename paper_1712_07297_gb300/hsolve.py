@@ -66,6 +66,7 @@ EXPORTS = {
     "hsolve_analyze": (C.c_int, [C.POINTER(Csr), C.c_void_p, C.c_int, C.POINTER(Opts), C.c_void_p,
                                  C.POINTER(C.c_void_p)]),
     "hsolve_factor": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "hsolve_factor_forced": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int32]),
     "hsolve_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int64]),
     "hsolve_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int64]),
     "hsolve_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
@@ -216,6 +217,17 @@ class Solver:
     def factor(self, eps: float, precision="fp64"):
         p = PRECISION[precision] if isinstance(precision, str) else int(precision)
         _check(load().hsolve_factor(self.h, float(eps), p), self.h)
+
+    def factor_forced(self, precision, ranks_per_level):
+        """Factor with every cluster's rank fixed (hsolve_factor_forced):
+        ranks_per_level[l] = the ranks of level l's clusters."""
+        import numpy as np
+        p = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        counts = np.array([len(r) for r in ranks_per_level], dtype=np.int32)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(r, dtype=np.int32)
+                                                    for r in ranks_per_level]))
+        _check(load().hsolve_factor_forced(self.h, p, flat.ctypes.data, counts.ctypes.data,
+                                           len(counts)), self.h)
 
     def apply(self, rhs, out=None):
         """out = M^{-1} rhs on the device (torch float64 CUDA tensors)."""

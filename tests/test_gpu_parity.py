@@ -368,3 +368,29 @@ def test_tensor_core_precisions(hs, precision, name, mk, leaf, eps, top):
         assert np.linalg.norm(b[c] - A @ x[c]) <= 1.0001e-10 * np.linalg.norm(b[c])
     assert info.iterations <= 2 * info64.iterations + 2, (info.iterations, info64.iterations)
     s.close()
+
+
+# At ranks forced to the oracle's (hsolve_factor_forced), the float32
+# factorization is the oracle's approximation in float32 arithmetic: M^{-1} b
+# agrees to 1e-5 relative (float32 rounding, 6e-8 per operation, grown by the
+# conditioning of the cluster blocks over the levels) -- the bound the
+# float32 blocks are held to -- and the float64 one to 1e-10.  The 10^6
+# contrast variable-coefficient case is factored as S A S (the equilibration
+# option, and the oracle on S A S): unscaled, its cluster blocks' conditioning
+# takes float32 to 7e-5.
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-10), ("mixed_fp32", 1e-5)])
+@pytest.mark.parametrize("name,mk,leaf,eps", CASES[:4])
+def test_forced_ranks_match_oracle(hs, precision, bound, name, mk, leaf, eps):
+    p = mk()
+    equil = name.startswith("vcdiff")
+    q, S = _equilibrated(p) if equil else (p, np.ones(p.n))
+    fac = _oracle(q, leaf, eps)
+    ranks = [np.asarray(lv.ranks, dtype=np.int32) for lv in fac.levels if lv.top is None]
+    s = hs.Solver.from_problem(p, leaf_size=leaf, symmetric=1, equilibrate=int(equil))
+    s.factor_forced(precision, ranks)
+    assert _ranks_match(s, fac) >= 1
+    b = I.rhs(p.n, 2, seed=1006)
+    ref = S[None, :] * H.solve(fac, (S[None, :] * b).T).T
+    out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(out, ref) < bound, _rel(out, ref)
+    s.close()
