@@ -251,6 +251,13 @@ struct Launch {
 };
 
 // float64 Krylov helpers (kernels.cu)
+// A run of consecutive vector slots: out[dst + q] = src + q for q < w.
+struct VRun {
+  int64_t dst, src;
+  int w, pad;
+};
+void expand_runs(const VRun* runs, int64_t nrun, int64_t* out, cudaStream_t st);
+
 void spmv_csr(int64_t n, const int64_t* rp, const int* ci, const double* v, const double* x,
               int64_t ldx, double* y, int64_t ldy, int nrhs, cudaStream_t st);
 void dots(int64_t n, const double* a, int64_t lda, const double* b, int64_t ldb, int nrhs,

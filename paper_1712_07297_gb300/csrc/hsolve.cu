@@ -507,12 +507,10 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   }
   int* rank = d_rank.as<int>();
   std::vector<ApplyRec> recs(nc);
-  std::vector<int64_t> vmap;
-  {
-    int64_t wsum = 0;
-    for (int s = 0; s < nc; s++) wsum += wmax[s];
-    vmap.reserve((size_t)wsum);  // one slot per neighbour unknown, at most
-  }
+  // the level's neighbour-slot map as runs (one per neighbour block of a
+  // cluster), expanded on the device at the end of the level
+  std::vector<VRun> vruns;
+  int64_t vmap_n = 0;
   std::vector<int> fillcols(nc, 0), fillw(nc, 0), nzcols(nc, -1);
   FL.cls.clear();
   // rank-independent part of every cluster's tasks, built in parallel: its
@@ -771,9 +769,11 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       r.voff = P.voff[s];
       r.T = oT[s]; r.TR = sym ? oT[s] : oTR[s];
       r.Y = oY[s]; r.XT = sym ? oY[s] : oXT[s];
-      r.map = (int64_t)vmap.size();
-      for (auto& e : N)
-        for (int q = 0; q < e.w; q++) vmap.push_back(P.voff[e.j] + q);
+      r.map = vmap_n;
+      for (auto& e : N) {
+        vruns.push_back({vmap_n, P.voff[e.j], e.w, 0});
+        vmap_n += e.w;
+      }
     }
     // ---- upload this class's task arrays
     Blob b;
@@ -965,10 +965,15 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   HostTimer ht_end(h, "host.level_end");
   Blob b;
   FL.recs.alloc(sizeof(ApplyRec) * std::max(nc, 1));
-  FL.vmap.alloc(sizeof(int64_t) * std::max<size_t>(vmap.size(), 1));
-  if (!vmap.empty())
-    HS_CUDA(cudaMemcpyAsync(FL.vmap.p, vmap.data(), sizeof(int64_t) * vmap.size(),
+  FL.vmap.alloc(sizeof(int64_t) * std::max<int64_t>(vmap_n, 1));
+  DevBuf d_vruns;  // kept until the level's final synchronisation below
+  if (!vruns.empty()) {
+    d_vruns.alloc(sizeof(VRun) * vruns.size());
+    HS_CUDA(cudaMemcpyAsync(d_vruns.p, vruns.data(), sizeof(VRun) * vruns.size(),
                             cudaMemcpyHostToDevice, h->st));
+    expand_runs(d_vruns.as<VRun>(), (int64_t)vruns.size(), FL.vmap.as<int64_t>(), h->st);
+    HS_CUDA(cudaGetLastError());
+  }
   std::vector<int> ids;
   FL.cls_off.clear();
   FL.cls_maxm.clear();

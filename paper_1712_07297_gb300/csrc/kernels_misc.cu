@@ -562,6 +562,22 @@ void Launch<real>::perm_out(const int64_t* perm, const double* S, int64_t n, con
 template struct Launch<double>;
 template struct Launch<float>;
 
+namespace {
+__global__ void expand_runs_kernel(const VRun* __restrict__ runs, int64_t nrun,
+                                   int64_t* __restrict__ out) {
+  for (int64_t r = blockIdx.x; r < nrun; r += gridDim.x) {
+    const VRun v = runs[r];
+    for (int q = threadIdx.x; q < v.w; q += blockDim.x) out[v.dst + q] = v.src + q;
+  }
+}
+}  // namespace
+
+void expand_runs(const VRun* runs, int64_t nrun, int64_t* out, cudaStream_t st) {
+  if (nrun <= 0) return;
+  count_launch();
+  expand_runs_kernel<<<(int)std::min<int64_t>(nrun, 152 * 32), 128, 0, st>>>(runs, nrun, out);
+}
+
 void spmv_csr(int64_t n, const int64_t* rp, const int* ci, const double* v, const double* x,
               int64_t ldx, double* y, int64_t ldy, int nrhs, cudaStream_t st) {
   count_launch();
