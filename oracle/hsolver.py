@@ -12,7 +12,7 @@ splits pi_s into fine and coarse DOFs, the elimination operator G_s (Eq.
 elim) removes the fine ones, and P_s (Eq. perm) leaves the coarse ones to the
 next level, where siblings of the bisection tree merge (Alg. 1, recursion).
 
-Readings of points the paper leaves open (each is also listed in the design doc):
+Readings of points the paper leaves open:
   * Clustering: recursive coordinate bisection to a uniform depth; each node
     is split at the median of its longest bounding-box axis (ties: lowest
     axis), ordering points by (coordinate, global index); the left half gets
@@ -34,7 +34,7 @@ Readings of points the paper leaves open (each is also listed in the design doc):
     diagonal block is zero in exact arithmetic; without this floor its
     "rank" is decided by rounding noise), or when the remaining columns are
     all exactly zero.  k = number of kept steps, U = first k columns of Q.
-  * Randomized variant (north_star's "randomized rank-revealing QR"): when
+  * Randomized variant (a randomized rank-revealing QR): when
     G has more than m + 8 columns, the same truncated pivoted QR runs on the
     sketch G Omega with Omega[q, j] = +-1/sqrt(m + 8), signs from the top
     bit of splitmix64((q << 32) | j), q the gathered column position.  With
