@@ -75,9 +75,11 @@ typedef struct {
                              below it); default 128 */
   int32_t symmetric;      /* -1 = detect (exact value symmetry), 0 = general
                              (LU, two-sided compression), 1 = SPD (Cholesky) */
-  int64_t top_size;       /* factor a level densely once it holds at most
-                             this many unknowns (0 = only when one cluster is
-                             left); default 0 */
+  int64_t top_size;       /* SPD matrices: factor a level densely once it
+                             holds at most this many unknowns (0 = only when
+                             one cluster is left); general matrices always
+                             keep the hierarchy down to one cluster; default
+                             0 */
   int32_t max_rank;       /* > 0: cap every compression rank at this value
                              (the fixed-rank option of Sec. 5.1); 0 = none */
   int32_t gmres_restart;  /* GMRES restart length; default 50 */

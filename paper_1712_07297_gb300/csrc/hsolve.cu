@@ -1134,7 +1134,9 @@ void factor_impl(hsolve_handle* h, double eps) {
     int live = 0;
     for (int i = 0; i < P.nclu; i++) live += P.m[i] > 0;
     const int64_t vlen = P.voff[P.nclu];
-    const bool small = (P.nclu == 1 || live <= 1 || vlen <= h->opts.top_size);
+    // top_size merges an SPD level into the dense top (blocked Cholesky);
+    // a general matrix keeps the hierarchy down to one cluster
+    const bool small = (P.nclu == 1 || live <= 1 || (h->symmetric && vlen <= h->opts.top_size));
     if (small && !(P.nclu == 1)) {
       // merge everything into one cluster for the dense top factor
       std::unique_ptr<FLevel> nxt;
