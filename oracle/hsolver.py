@@ -321,6 +321,12 @@ class ClusterFactor:
     rdiag: list
     margin: float
     ncols_fill: int         # nonzero columns of G
+    # recorded for comparisons with other implementations (no later step
+    # reads them): A_ss as the cluster met it, its new coarse rows
+    # U^T A_ss^{-1} A_sN (k x sum width) and coarse columns A_Ns A_ss^{-1} U
+    Ass: np.ndarray | None = None
+    Yc: np.ndarray | None = None
+    Xc: np.ndarray | None = None
 
 
 @dataclasses.dataclass
@@ -414,18 +420,21 @@ def _process_cluster(s, blocks, cur, adj, d2, eps, symmetric, max_rank, compress
     widths = [(n, cur[n]) for n in N]
     AsN = np.hstack([blocks[(s, n)][:m, :w] for n, w in widths]) if N else np.zeros((m, 0))
     ANs = np.vstack([blocks[(n, s)][:w, :m] for n, w in widths]) if N else np.zeros((0, m))
+    Ass0 = Ass.copy()
     if k == m:
         # untouched: all DOFs coarse, E_s = I
         return ClusterFactor(s, m, m, None, None, np.zeros((0, 0)), np.zeros((0, 0)),
                              np.zeros(0, dtype=np.int64), widths, np.zeros((AsN.shape[1], 0)),
                              np.zeros((0, AsN.shape[1])), cp["piv"], cp["rdiag"], cp["margin"],
-                             G.shape[1])
+                             G.shape[1], Ass0)
     if k == 0:
         # no fill kept: E_s = I, plain block elimination (Sec. 2.2)
         TL = TR = None
         F = Ass.copy()
         R = AsN
         Cn = ANs
+        Yc = np.zeros((0, AsN.shape[1]))
+        Xc = np.zeros((ANs.shape[0], 0))
     else:
         U = cp["U"]
         B = np.linalg.solve(Ass, np.eye(m))          # A_ss^{-1}
@@ -439,6 +448,8 @@ def _process_cluster(s, blocks, cur, adj, d2, eps, symmetric, max_rank, compress
         X = Y.T if symmetric else ANs @ TR            # [A_Ns B U, A_Ns B V_R]
         R = Y[k:]
         Cn = X[:, k:]
+        Yc = Y[:k].copy()
+        Xc = X[:, :k].copy()
         # new coarse rows/cols of s (Eq. scaling, display)
         col0 = 0
         for n, w in widths:
@@ -475,7 +486,7 @@ def _process_cluster(s, blocks, cur, adj, d2, eps, symmetric, max_rank, compress
             c0 += w2
         r0 += w1
     return ClusterFactor(s, m, k, TL, TR, LF, UF, PF, widths, BL, BR, cp["piv"], cp["rdiag"],
-                         cp["margin"], G.shape[1])
+                         cp["margin"], G.shape[1], Ass0, Yc, Xc)
 
 
 def factor(prob_rowptr, prob_col, prob_val, coords, leaf: int, eps: float,
@@ -539,6 +550,55 @@ def factor(prob_rowptr, prob_col, prob_val, coords, leaf: int, eps: float,
         sizes = nsizes
         nclu = nxt
     return Factorization(len(prob_rowptr) - 1, symmetric, perm, levels)
+
+
+def stored_operators(cf: ClusterFactor, symmetric: bool):
+    """The operators of one processed cluster in the form an implementation
+    that folds the fine block's factors into the sparsification rows stores
+    them (Eqs. scaling and elim combined):
+
+      T   = [U^T A_ss^{-1}; L_F^{-1} P_F V_L^T A_ss^{-1}]       (m x m)
+      TRt = [U^T A_ss^{-T}; U_F^{-T} V_R^T A_ss^{-T}]           (general)
+      Y   = [U^T A_ss^{-1} A_sN; B_R]                          (m x sum width)
+      XT  = [(A_Ns A_ss^{-1} U)^T; B_L^T]                      (general)
+
+    With k = 0 (E_s = I) the sparsification rows are the identity: T =
+    L_F^{-1} P_F and TRt = U_F^{-T} for F = A_ss.  A cluster with k = m keeps
+    no operators (returns None)."""
+    m, k = cf.m, cf.k
+    if k == m:
+        return None
+    f = m - k
+    unit = not symmetric
+    if cf.TL is None:
+        TL = np.eye(m)
+        TRm = np.eye(m)
+    else:
+        TL = cf.TL
+        TRm = cf.TL.T if symmetric else cf.TR
+    T = np.vstack([TL[:k], sla.solve_triangular(cf.LF, TL[k:][cf.PF], lower=True,
+                                                 unit_diagonal=unit)])
+    Y = np.vstack([cf.Yc, cf.BR])
+    out = dict(T=T, Y=Y, TRt=None, XT=None)
+    if not symmetric:
+        out["TRt"] = np.vstack([TRm[:, :k].T,
+                                sla.solve_triangular(cf.UF.T, TRm[:, k:].T, lower=True)])
+        out["XT"] = np.vstack([cf.Xc.T, cf.BL.T])
+    assert T.shape == (m, m) and Y.shape[0] == m and cf.BR.shape[0] == f
+    return out
+
+
+def top_operators(top: dict):
+    """The dense top in the same form: T = L^{-1} (Cholesky A = L L^T) or,
+    for an LU top A = P L U, T = L^{-1} P^T and TRt = U^{-T}.  An empty top
+    (no unknown left) has none (returns None)."""
+    n = top["n"]
+    if n == 0:
+        return None
+    if top["kind"] == "chol":
+        return dict(T=sla.solve_triangular(top["L"], np.eye(n), lower=True), TRt=None)
+    T = sla.solve_triangular(top["L"], top["P"].T, lower=True, unit_diagonal=True)
+    return dict(T=T, TRt=sla.solve_triangular(top["U"].T, np.eye(n), lower=True))
 
 
 # ---------------------------------------------------------------------------

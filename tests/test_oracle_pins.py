@@ -337,3 +337,112 @@ def test_smallest_last_order_by_definition():
     for i in range(n):
         assert all(col[i] != col[j] for j in nb[i])
         assert col[i] <= len(nb[i])
+
+
+# ---------------------------------------------------------------------------
+# The stored operators (the form the library exports, Eqs. scaling + elim)
+# ---------------------------------------------------------------------------
+
+def _stored_cases():
+    return [
+        (I.poisson((20, 20)), 16, 1e-2, True),
+        (I.poisson((8, 8, 8)), 32, 1e-2, True),
+        (I.convection_diffusion((14, 12), 10.0), 16, 1e-2, False),
+    ]
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_stored_operators_block_diagonalise(case):
+    # T' A_ss T'_R = diag(C, I_f) with C = U^T A_ss^{-1} U: the sparsification
+    # operator decouples coarse from fine unknowns (V^T A_ss^{-1} U = 0) and
+    # the folded factors of F turn the fine block into the identity
+    p, leaf, eps, sym = _stored_cases()[case]
+    fac = H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=sym)
+    seen = 0
+    for lv in fac.levels:
+        if lv.top is not None:
+            op = H.top_operators(lv.top)
+            if op is not None:
+                A = (lv.top["L"] @ lv.top["L"].T if lv.top["kind"] == "chol"
+                     else lv.top["P"] @ lv.top["L"] @ lv.top["U"])
+                TR = op["T"].T if op["TRt"] is None else op["TRt"].T
+                assert np.abs(op["T"] @ A @ TR - np.eye(lv.top["n"])).max() < 1e-12
+            continue
+        for cf in lv.factors.values():
+            op = H.stored_operators(cf, sym)
+            if op is None:
+                continue
+            T = op["T"]
+            TR = T.T if sym else op["TRt"].T
+            k, f = cf.k, cf.m - cf.k
+            D = T @ cf.Ass @ TR
+            if cf.TL is None:  # k = 0: no coarse block
+                C = np.zeros((0, 0))
+            else:
+                C = cf.TL[:k] @ cf.Ass @ (cf.TL[:k].T if sym else cf.TR[:, :k])
+            scale = max(np.abs(D).max(), 1.0)
+            assert np.abs(D[:k, :k] - C).max(initial=0) <= 1e-12 * scale
+            assert np.abs(D[:k, k:]).max(initial=0) <= 1e-12 * scale
+            assert np.abs(D[k:, :k]).max(initial=0) <= 1e-12 * scale
+            assert np.abs(D[k:, k:] - np.eye(f)).max(initial=0) <= 1e-12 * scale
+            assert np.array_equal(op["Y"][k:], cf.BR)
+            seen += 1
+    assert seen > 3
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_stored_operators_reproduce_the_solve(case):
+    # Alg. 2 written with the stored operators only (forward z_s = T' y_s,
+    # y_N -= (B_L rows) z_f; backward z_f = x_f - B_R x_N, x_s = T'_R z)
+    # must give the oracle's M^{-1} b: a transposed, permuted or dropped piece
+    # of T', T'_R, Y or X^T changes the result
+    p, leaf, eps, sym = _stored_cases()[case]
+    fac = H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=sym)
+    b = I.rhs(p.n, 2, seed=11).T
+    ref = H.solve(fac, b)
+    y = b[fac.perm].copy()
+    stack = []
+    for lv in fac.levels:
+        if lv.top is not None:
+            op = H.top_operators(lv.top)
+            if op is not None:
+                z = op["T"] @ y
+                y = (op["T"].T if op["TRt"] is None else op["TRt"].T) @ z
+            break
+        for s in lv.order:
+            cf = lv.factors.get(s)
+            op = None if cf is None else H.stored_operators(cf, sym)
+            if op is None:
+                continue
+            o = lv.offsets[s]
+            z = op["T"] @ y[o:o + cf.m]
+            BLt = (op["Y"] if sym else op["XT"])[cf.k:]
+            c0 = 0
+            for n, w in cf.nbrs:
+                on = lv.offsets[n]
+                y[on:on + w] -= BLt[:, c0:c0 + w].T @ z[cf.k:]
+                c0 += w
+            y[o:o + cf.m] = z
+        stack.append(y)
+        y = H._gather_next(lv, y)
+    for lv in reversed([l for l in fac.levels if l.top is None]):
+        yl = stack.pop()
+        H._scatter_next(lv, yl, y)
+        for s in reversed(lv.order):
+            cf = lv.factors.get(s)
+            op = None if cf is None else H.stored_operators(cf, sym)
+            if op is None:
+                continue
+            o = lv.offsets[s]
+            z = yl[o:o + cf.m].copy()
+            c0 = 0
+            for n, w in cf.nbrs:
+                on = lv.offsets[n]
+                z[cf.k:] -= op["Y"][cf.k:, c0:c0 + w] @ yl[on:on + w]
+                c0 += w
+            TRt = op["T"] if sym else op["TRt"]
+            yl[o:o + cf.m] = TRt.T @ z
+        y = yl
+    x = np.empty_like(b)
+    x[fac.perm] = y
+    assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
