@@ -163,16 +163,20 @@ hsolve_status hsolve_factor(hsolve_handle* h, double eps, hsolve_precision prec)
 /* Test entry point: hsolve_factor with the rank of every cluster fixed in
  * advance (Eq. lra keeps exactly that many pivoted-QR directions, fewer only
  * where the fill block has no more nonzero ones; neither eps nor the
- * rounding-noise floor plays a part), so that
- * a float32 factorization can be compared with a float64 reference at
- * identical ranks.  ranks: the per-cluster ranks of levels 0..nlevels-1
- * concatenated (clusters in index order); counts[l]: clusters of level l,
- * which must equal the level's cluster count (HSOLVE_ERR_ARG otherwise).
- * Levels beyond nlevels (and the dense top) are factored as usual with
- * eps = 0.  Host pointers; copied. */
+ * rounding-noise floor plays a part), and optionally the pivot order of every
+ * cluster's pivoted QR too, so that a float32 factorization can be compared
+ * block by block with a float64 reference at identical ranks and pivots (a
+ * float32 search can legitimately break near-ties of the column norms the
+ * other way, which changes the basis U).  ranks: the per-cluster ranks of
+ * levels 0..nlevels-1 concatenated (clusters in index order); counts[l]:
+ * clusters of level l, which must equal the level's cluster count
+ * (HSOLVE_ERR_ARG otherwise).  pivots (may be NULL = search as usual): for
+ * every level and cluster in the same order, ranks[s] column indices in the
+ * numbering of hsolve_export_level's pivot array.  Levels beyond nlevels (and
+ * the dense top) are factored as usual with eps = 0.  Host pointers; copied. */
 hsolve_status hsolve_factor_forced(hsolve_handle* h, hsolve_precision prec,
                                    const int32_t* ranks, const int32_t* counts,
-                                   int32_t nlevels);
+                                   int32_t nlevels, const int32_t* pivots);
 
 /* Preconditioner application (Alg. 2): out = M^{-1} rhs where M is the
  * factorization.  rhs and out are DEVICE pointers, column-major n x nrhs with
@@ -196,7 +200,10 @@ hsolve_status hsolve_apply(hsolve_handle* h, const double* rhs, double* out,
  * library holds until the process exits.
  * - The first call on a device looks up that array's device address (with
  *   the device current) and caches it; make that first call before any
- *   stream capture.
+ *   stream capture.  The CUDA runtime may also load the library's kernels
+ *   into device memory on their first launch (lazy module loading), which
+ *   the library does not control; after that, calls leave the device's
+ *   free memory unchanged.
  * - All calls share the array and it keeps the last call's contents; calls
  *   whose device work overlaps in time (other streams, other handles) race
  *   on it, so serialise them.
@@ -246,6 +253,18 @@ hsolve_status hsolve_tc_gemm(int mode, int M, int N, int K, const float* A,
                              int64_t rsa, int64_t csa, const float* B,
                              int64_t rsb, int64_t csb, float* C, int64_t ldc,
                              float alpha, float beta, int lower, void* stream);
+
+/* Diagnostic of the library's bounded device waits (the paper has no
+ * counterpart: every wait of the library's kernels gives up after about a
+ * second and reports HSOLVE_ERR_TIMEOUT instead of hanging).  Runs one wait
+ * of the given kind with a limit of limit_cycles SM clocks on something that
+ * nothing signals -- kind 0: the mbarrier wait of the tensor-core kernels
+ * (the only kind) -- and returns the status the kernel recorded:
+ * HSOLVE_ERR_TIMEOUT when the wait gave up as designed.  The device stays
+ * usable afterwards.  stream: a cudaStream_t (NULL = default stream).
+ * Errors: HSOLVE_ERR_ARG (another kind, negative limit), HSOLVE_ERR_OOM,
+ * HSOLVE_ERR_CUDA. */
+hsolve_status hsolve_wait_selftest(int kind, int64_t limit_cycles, void* stream);
 
 /* ---- Serving runtime (a request loop over the solver; the paper has no
  * counterpart: it is the service form of factoring once and solving many
@@ -336,6 +355,62 @@ hsolve_status hsolve_get_stats(const hsolve_handle* h, hsolve_stats* out);
 hsolve_status hsolve_get_level(const hsolve_handle* h, int level, int32_t* nclu,
                                int32_t* sizes, int32_t* ranks, int32_t* colour,
                                int32_t cap);
+
+/* ---- Export of a factored level (for parity tests against a reference
+ * implementation of Alg. 1).  For every cluster s processed at the level,
+ * the factorization keeps (Sec. 2.1, Eqs. lra, scaling, elim):
+ *   T'  = [U^T A_ss^{-1}; L_F^{-1} P_F V_L^T A_ss^{-1}]   (m x m)
+ *         the sparsification rows with the inverse factor of the fine block
+ *         F = V_L^T A_ss^{-1} V_R folded into the fine ones; with k = 0
+ *         (no fill kept) T' = L^{-1} P of A_ss = P^T L U (L^{-1} for SPD);
+ *         for the dense top T' = L^{-1} of its Cholesky factor;
+ *   T'_R^T (general only) = [U^T A_ss^{-T}; U_F^{-T} V_R^T A_ss^{-T}];
+ *   Y   = T' A_sN (m x nw): rows 0..k are the cluster's new coarse rows
+ *         U^T A_ss^{-1} A_sN, rows k..m are B_R = L_F^{-1} P_F V_L^T A_ss^{-1} A_sN;
+ *   X^T (general only) = T'_R^T A_Ns^T: rows k..m are B_L^T;
+ * where N are the cluster's neighbours (ascending id, width = their current
+ * unknowns) and U the first k directions of the column-pivoted QR of its fill
+ * block.  The pivot order of that QR is kept too: entry j is the column
+ * chosen at step j, counted among the nonzero columns of the gathered fill
+ * block [A_sw] (SPD) or [A_sw, A_ws^T] (general) with w ascending (among
+ * the sketch columns for the randomized variant). */
+typedef struct {
+  int32_t m;          /* unknowns when processed; 0: not processed here */
+  int32_t k;          /* coarse unknowns kept (the rank of Eq. lra) */
+  int32_t nw;         /* columns of Y: sum of the neighbours' widths */
+  int32_t nnb;        /* neighbours */
+  int32_t colour;     /* colour class; clusters run in (colour, id) order */
+  int32_t npiv;       /* pivots recorded (= k) */
+  int64_t T;          /* offset of T' in the exported factor array, or -1
+                         (not processed, or k = m: the cluster is untouched) */
+  int64_t TR;         /* offset of T'_R^T (general), else -1 */
+  int64_t Y;          /* offset of Y (column-major, ld m), or -1 */
+  int64_t XT;         /* offset of X^T (general, ld m), else -1 */
+  int64_t piv;        /* offset of the pivots in the pivot array */
+  int64_t nb;         /* offset of the neighbours in nbr_id / nbr_w */
+} hsolve_cluster_export;
+
+typedef struct {
+  int32_t nclu;       /* clusters of the level */
+  int32_t dense_top;  /* 1: the level is the dense top (one cluster) */
+  int32_t symmetric;  /* 1: SPD path (Cholesky, one-sided operators) */
+  int32_t precision;  /* hsolve_precision of the stored blocks */
+  int64_t fac_elems;  /* elements of the factor array */
+  int64_t piv_total;  /* entries of the pivot array */
+  int64_t nbr_total;  /* entries of nbr_id / nbr_w */
+} hsolve_level_export;
+
+/* Export level `level` (0 = leaves) of the current factorization: sizes into
+ * *info (required), and, where the pointer is not NULL, nclu cluster
+ * records, the factor array (fac_elems entries, converted to float64), the
+ * pivots (piv_total) and the neighbour ids and widths (nbr_total each).  All
+ * pointers are HOST memory owned by the caller; call once with NULLs to learn
+ * the sizes.  A level that only merged clusters into the dense top reports
+ * nclu clusters that were not processed.  Errors: HSOLVE_ERR_ARG (level out
+ * of range), HSOLVE_ERR_STATE (no factorization), HSOLVE_ERR_CUDA. */
+hsolve_status hsolve_export_level(const hsolve_handle* h, int level, hsolve_level_export* info,
+                                  hsolve_cluster_export* clusters, double* fac,
+                                  int32_t* pivots, int32_t* nbr_id, int32_t* nbr_w);
 
 /* Level-0 cluster of every unknown: perm[p] = global index of the unknown at
  * position p of the cluster-ordered vector (host array of n entries). */

@@ -116,6 +116,9 @@ struct PrepTask {
   int64_t Y;        // workspace offset of the sketch Y (ld m)
   int ngcol;        // number of fill-column runs
   int pad2;
+  int64_t pv;       // offset in the level's pivot array: the column chosen at
+                    // step j of the pivoted QR goes to pv + j (index among the
+                    // nonzero gathered columns, or among the sketch columns)
 };
 
 // Sketch task: Y (m x l, ld m) = G Omega for the gathered fill columns of
@@ -179,6 +182,11 @@ struct ApplyRec {   // one cluster's factor, as the substitution sweeps use it
   int64_t part;     // offset of the backward partial sums (per right-hand side)
 };
 
+// Diagnostic of the bounded mbarrier wait of the tensor-core kernels: waits,
+// with `limit` SM clocks, on a barrier nothing arrives at and records
+// HSOLVE_ERR_TIMEOUT in *err.
+void mbar_wait_probe(long long limit, int* err, cudaStream_t st);
+
 // Tensor-core products (kernels_tc.cu).  mode 0 = TF32, 1 = 3xTF32 (hi/lo
 // split), 2 = BF16 operands; float32 accumulation.  C = beta C + alpha A B^T
 // with A: M x K (element (r, k) at A[r * rsa + k * csa]), B: N x K likewise,
@@ -201,7 +209,8 @@ template <typename real>
 struct Launch {
   static void prep(const PrepTask* tasks_dev, int ntask, real* arena, real* fac,
                    real* ws, double* wsd, const Seg* segs,
-                   int* rank, double eps, int sym, int max_rank, int maxm,
+                   int* rank, int* piv, const int* fpiv, double eps, int sym, int max_rank,
+                   int maxm,
                    DevError* err, int level, long long* dbg, cudaStream_t st);
   // thread-block-cluster pivoted QR: cluster size for the largest task (0 =
   // does not fit), its dynamic shared memory, and the launch
@@ -211,7 +220,8 @@ struct Launch {
                        double* wsd, const Seg* segs, int* cnt, cudaStream_t st);
   static void qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, int maxc, int CL,
                          const real* arena, real* ws, double* wsd, const Seg* segs, int* rank,
-                         const int* cnt, double eps, int max_rank, cudaStream_t st);
+                         int* piv, const int* fpiv, const int* cnt, double eps, int max_rank,
+                         cudaStream_t st);
   static void sketch(const SketchTask* tasks_dev, int ntask, int maxm, int maxl,
                      const real* arena, real* ws, const Seg* segs,
                      cudaStream_t st);
@@ -262,10 +272,13 @@ void spmv_csr(int64_t n, const int64_t* rp, const int* ci, const double* v, cons
               int64_t ldx, double* y, int64_t ldy, int nrhs, cudaStream_t st);
 void dots(int64_t n, const double* a, int64_t lda, const double* b, int64_t ldb, int nrhs,
           double* out, cudaStream_t st);
-void multi_dot(int64_t n, int nv, const double* V, int64_t ldv, const double* w, double* out,
-               cudaStream_t st);
-void multi_axpy(int64_t n, int nv, const double* V, int64_t ldv, const double* coef,
-                double sign, double* w, cudaStream_t st);
+// Block Krylov helpers: nv blocks V_i of n x nrhs (ld n, block stride
+// n * nrhs).  out[(nv*nrhs) * kDotBlocks + i * nrhs + c] = V_i[:, c] . w[:, c]
+// (partials before it); w[:, c] += sign sum_i coef[i * nrhs + c] V_i[:, c].
+void block_multi_dot(int64_t n, int nv, int nrhs, const double* V, const double* w,
+                     double* out, cudaStream_t st);
+void block_multi_axpy(int64_t n, int nv, int nrhs, const double* V, const double* coef,
+                      double sign, double* w, int64_t ldw, cudaStream_t st);
 void axpby_cols(int64_t n, int nrhs, const double* alpha, const double* x, int64_t ldx,
                 const double* beta, double* y, int64_t ldy, cudaStream_t st);
 

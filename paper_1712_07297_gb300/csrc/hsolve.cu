@@ -175,6 +175,13 @@ struct FLevel {
   DevBuf vec, zvec, part;             // level vector, scratch vector, partial sums
   int vec_nrhs = 0;
   bool top = false;
+  // kept for hsolve_export_level: the pivot order of every cluster's
+  // pivoted QR (int, at the cluster's slot offset), the host copy of the
+  // apply records, and each cluster's neighbours (id, width) in the column
+  // order of its neighbour blocks
+  DevBuf piv;
+  std::vector<ApplyRec> hrecs;
+  std::vector<int> nb_ptr, nb_id, nb_w;
 };
 
 }  // namespace
@@ -254,9 +261,12 @@ struct hsolve_handle {
     LevelPattern Q;
   };
   std::vector<PatCache> pcache;
-  // hsolve_factor_forced: per level, the rank of every cluster
+  // hsolve_factor_forced: per level, the rank of every cluster and (when
+  // given) the pivot order of every cluster's pivoted QR, concatenated in
+  // cluster order (rank entries each)
   bool force_ranks = false;
   std::vector<std::vector<int>> forced;
+  std::vector<std::vector<int>> forced_piv;
   std::string err;
 };
 
@@ -506,7 +516,35 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     HS_CUDA(cudaMemsetAsync(d_rank.p, 0, sizeof(int) * std::max(nc, 1), h->st));
   }
   int* rank = d_rank.as<int>();
+  FL.piv.alloc(sizeof(int) * std::max<int64_t>(P.voff[nc], 1));
+  int* pivd = FL.piv.as<int>();
+  // forced pivot orders: cluster s's list at its slot offset
+  DevBuf d_fpiv;
+  const int* fpiv = nullptr;
+  if (forced && level < (int)h->forced_piv.size()) {
+    std::vector<int> fp((size_t)std::max<int64_t>(P.voff[nc], 1), -1);
+    const std::vector<int>& src = h->forced_piv[level];
+    size_t o = 0;
+    for (int s = 0; s < nc; s++) {
+      const int k = h->forced[level][s];
+      if (k < 0 || k > P.m[s] || o + k > src.size())
+        throw Fail(HSOLVE_ERR_ARG, "forced pivots: level " + std::to_string(level) +
+                                       " has fewer entries than its ranks");
+      for (int j = 0; j < k; j++) fp[P.voff[s] + j] = src[o + j];
+      o += k;
+    }
+    if (o != src.size())
+      throw Fail(HSOLVE_ERR_ARG, "forced pivots: level " + std::to_string(level) +
+                                     " has more entries than its ranks");
+    d_fpiv.alloc(sizeof(int) * fp.size());
+    HS_CUDA(cudaMemcpyAsync(d_fpiv.p, fp.data(), sizeof(int) * fp.size(), cudaMemcpyHostToDevice,
+                            h->st));
+    HS_CUDA(cudaStreamSynchronize(h->st));  // the host vector is pageable
+    fpiv = d_fpiv.as<int>();
+  }
   std::vector<ApplyRec> recs(nc);
+  FL.nb_ptr.assign(nc + 1, 0);
+  std::vector<std::vector<std::pair<int, int>>> nbl(nc);
   // the level's neighbour-slot map as runs (one per neighbour block of a
   // cluster), expanded on the device at the end of the level
   std::vector<VRun> vruns;
@@ -663,6 +701,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       pt.a_ss = P.off[P.find(s, s)];
       pt.gcol = gcol;
       pt.ngcol = ngcol;
+      pt.pv = P.voff[s];
       pt.ws = ws_e;
       ws_e += 11 * mm + (int64_t)m * ncolG;
       pt.D = ws_e;
@@ -773,6 +812,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       for (auto& e : N) {
         vruns.push_back({vmap_n, P.voff[e.j], e.w, 0});
         vmap_n += e.w;
+        nbl[s].push_back({e.j, e.w});
       }
     }
     // ---- upload this class's task arrays
@@ -847,8 +887,8 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         d_prep = reinterpret_cast<const PrepTask*>(h->blob3.as<char>() + o3_prep);
         timed_lv(h, "qr_cluster", level, 1, [&] {
           Launch<real>::qr_cluster(d_qrt, (int)qrt.size(), qm, nzmax, CL, arena, ws,
-                                   h->wsd.as<double>(), d_segs, rank, h->cnt.as<int>(), eps,
-                                   max_rank_arg, h->st);
+                                   h->wsd.as<double>(), d_segs, rank, pivd, fpiv,
+                                   h->cnt.as<int>(), eps, max_rank_arg, h->st);
         });
       }
     }
@@ -865,7 +905,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     }
     timed_lv(h, "prep", level, 1, [&] {
       Launch<real>::prep(d_prep, nt, arena, fac, ws,
-                         h->wsd.as<double>(), d_segs, rank, eps, sym ? 1 : 0,
+                         h->wsd.as<double>(), d_segs, rank, pivd, fpiv, eps, sym ? 1 : 0,
                          max_rank_arg, maxm, h->d_err.as<DevError>(), level, dbg, h->st);
     });
     if (dbg) {
@@ -996,6 +1036,16 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   }
   HS_CUDA(cudaMemcpyAsync(FL.recs.p, recs.data(), sizeof(ApplyRec) * nc, cudaMemcpyHostToDevice,
                           h->st));
+  FL.hrecs = recs;
+  FL.nb_id.clear();
+  FL.nb_w.clear();
+  for (int s = 0; s < nc; s++) {
+    for (auto& e : nbl[s]) {
+      FL.nb_id.push_back(e.first);
+      FL.nb_w.push_back(e.second);
+    }
+    FL.nb_ptr[s + 1] = (int)FL.nb_id.size();
+  }
   FL.cls_off.push_back((int)ids.size());
   FL.ids.alloc(sizeof(int) * std::max<size_t>(ids.size(), 1));
   if (!ids.empty())
@@ -1190,24 +1240,34 @@ void factor_impl(hsolve_handle* h, double eps) {
 // ---------------------------------------------------------------------------
 // Substitution (Alg. 2)
 // ---------------------------------------------------------------------------
+// The vectors one application of the sweeps works in, per level: the level
+// vector, a scratch vector and the backward partial sums.
+struct LevelVecs {
+  void* vec;
+  void* zvec;
+  void* part;
+};
+
 // The level sweeps of Alg. 2 between the level-0 vector and itself: a fixed
-// sequence of launches once the factorization and nrhs are fixed.
+// sequence of launches once the factorization and nrhs are fixed (one group
+// of launches per colour class and direction).
 template <typename real>
-void apply_levels(hsolve_handle* h, int nrhs, cudaStream_t st) {
+void apply_levels(hsolve_handle* h, int nrhs, cudaStream_t st, const std::vector<LevelVecs>& B) {
   const int L = (int)h->F.size();
+  auto vec = [&](int l) { return static_cast<real*>(B[l].vec); };
   for (int l = 0; l < L; l++) {
     FLevel& F = *h->F[l];
     const int64_t nl = std::max<int64_t>(F.P.voff[F.P.nclu], 1);
     for (size_t c = 0; c < F.cls.size(); c++)
       Launch<real>::apply_fwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
                               (int)F.cls[c].size(), F.cls_maxm[c], F.cls_maxnw[c],
-                              F.fac.as<real>(), F.vmap.as<int64_t>(), F.vec.as<real>(),
-                              F.zvec.as<real>(), nl, nrhs, st);
+                              F.fac.as<real>(), F.vmap.as<int64_t>(), vec(l),
+                              static_cast<real*>(B[l].zvec), nl, nrhs, st);
     if (l + 1 < L) {
       FLevel& G = *h->F[l + 1];
       const int64_t ng = std::max<int64_t>(G.P.voff[G.P.nclu], 1);
-      Launch<real>::gather_vec(F.next_idx.as<int64_t>(), F.next_n, F.vec.as<real>(), nl,
-                               G.vec.as<real>(), ng, nrhs, st);
+      Launch<real>::gather_vec(F.next_idx.as<int64_t>(), F.next_n, vec(l), nl, vec(l + 1), ng,
+                               nrhs, st);
     }
   }
   for (int l = L - 1; l >= 0; l--) {
@@ -1216,14 +1276,15 @@ void apply_levels(hsolve_handle* h, int nrhs, cudaStream_t st) {
     if (l + 1 < L) {
       FLevel& G = *h->F[l + 1];
       const int64_t ng = std::max<int64_t>(G.P.voff[G.P.nclu], 1);
-      Launch<real>::scatter_vec(F.next_idx.as<int64_t>(), F.next_n, G.vec.as<real>(), ng,
-                                F.vec.as<real>(), nl, nrhs, st);
+      Launch<real>::scatter_vec(F.next_idx.as<int64_t>(), F.next_n, vec(l + 1), ng, vec(l), nl,
+                                nrhs, st);
     }
     for (int c = (int)F.cls.size() - 1; c >= 0; c--)
       Launch<real>::apply_bwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
                               (int)F.cls[c].size(), F.cls_maxm[c], F.cls_maxnw[c],
-                              F.fac.as<real>(), F.vmap.as<int64_t>(), F.vec.as<real>(),
-                              F.zvec.as<real>(), F.part.as<real>(), nl, nrhs, st);
+                              F.fac.as<real>(), F.vmap.as<int64_t>(), vec(l),
+                              static_cast<real*>(B[l].zvec), static_cast<real*>(B[l].part), nl,
+                              nrhs, st);
   }
 }
 
@@ -1241,11 +1302,13 @@ void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int6
     }
   }
   if (realloc) h->drop_graphs();
+  std::vector<LevelVecs> B;
+  for (auto& F : h->F) B.push_back({F->vec.p, F->zvec.p, F->part.p});
   FLevel& F0 = *h->F[0];
   const int64_t n0 = F0.P.voff[F0.P.nclu];
   Launch<real>::perm_in(h->d_perm.as<int64_t>(), hscale(h), h->n, rhs, ld, F0.vec.as<real>(), n0, nrhs, h->st);
   if (!h->use_graphs) {
-    apply_levels<real>(h, nrhs, h->st);
+    apply_levels<real>(h, nrhs, h->st, B);
   } else {
     // the sweeps are captured once per nrhs into a CUDA graph (on a private
     // stream: capture does not execute) and replayed on the caller's stream
@@ -1261,7 +1324,7 @@ void apply_impl(hsolve_handle* h, const double* rhs, double* out, int nrhs, int6
       }
       const int64_t l0 = launches_total();
       HS_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
-      apply_levels<real>(h, nrhs, h->cap_stream);
+      apply_levels<real>(h, nrhs, h->cap_stream, B);
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
       if (e != cudaSuccess) throw Fail(HSOLVE_ERR_CUDA, std::string("apply capture: ") + cudaGetErrorString(e));
@@ -1368,44 +1431,15 @@ void apply_scratch_impl(hsolve_handle* h, const double* rhs, double* out, int nr
                         unsigned char* base) {
   std::vector<size_t> offs;
   noalloc_layout<real>(h, nrhs, &offs);
-  const int L = (int)h->F.size();
-  auto vec = [&](int l) { return reinterpret_cast<real*>(base + offs[3 * l]); };
-  auto zv = [&](int l) { return reinterpret_cast<real*>(base + offs[3 * l + 1]); };
-  auto pt = [&](int l) { return reinterpret_cast<real*>(base + offs[3 * l + 2]); };
+  std::vector<LevelVecs> B;
+  for (size_t l = 0; l < h->F.size(); l++)
+    B.push_back({base + offs[3 * l], base + offs[3 * l + 1], base + offs[3 * l + 2]});
   FLevel& F0 = *h->F[0];
   const int64_t n0 = F0.P.voff[F0.P.nclu];
-  Launch<real>::perm_in(h->d_perm.as<int64_t>(), hscale(h), h->n, rhs, ld, vec(0), n0, nrhs, h->st);
-  for (int l = 0; l < L; l++) {
-    FLevel& F = *h->F[l];
-    const int64_t nl = std::max<int64_t>(F.P.voff[F.P.nclu], 1);
-    for (size_t c = 0; c < F.cls.size(); c++)
-      Launch<real>::apply_fwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
-                              (int)F.cls[c].size(), F.cls_maxm[c], F.cls_maxnw[c],
-                              F.fac.as<real>(), F.vmap.as<int64_t>(), vec(l), zv(l), nl, nrhs,
-                              h->st);
-    if (l + 1 < L) {
-      FLevel& G = *h->F[l + 1];
-      const int64_t ng = std::max<int64_t>(G.P.voff[G.P.nclu], 1);
-      Launch<real>::gather_vec(F.next_idx.as<int64_t>(), F.next_n, vec(l), nl, vec(l + 1), ng,
-                               nrhs, h->st);
-    }
-  }
-  for (int l = L - 1; l >= 0; l--) {
-    FLevel& F = *h->F[l];
-    const int64_t nl = std::max<int64_t>(F.P.voff[F.P.nclu], 1);
-    if (l + 1 < L) {
-      FLevel& G = *h->F[l + 1];
-      const int64_t ng = std::max<int64_t>(G.P.voff[G.P.nclu], 1);
-      Launch<real>::scatter_vec(F.next_idx.as<int64_t>(), F.next_n, vec(l + 1), ng, vec(l), nl,
-                                nrhs, h->st);
-    }
-    for (int c = (int)F.cls.size() - 1; c >= 0; c--)
-      Launch<real>::apply_bwd(F.recs.as<ApplyRec>(), F.ids.as<int>() + F.cls_off[c],
-                              (int)F.cls[c].size(), F.cls_maxm[c], F.cls_maxnw[c],
-                              F.fac.as<real>(), F.vmap.as<int64_t>(), vec(l), zv(l), pt(l), nl,
-                              nrhs, h->st);
-  }
-  Launch<real>::perm_out(h->d_perm.as<int64_t>(), hscale(h), h->n, vec(0), n0, out, ld, nrhs, h->st);
+  real* v0 = static_cast<real*>(B[0].vec);
+  Launch<real>::perm_in(h->d_perm.as<int64_t>(), hscale(h), h->n, rhs, ld, v0, n0, nrhs, h->st);
+  apply_levels<real>(h, nrhs, h->st, B);
+  Launch<real>::perm_out(h->d_perm.as<int64_t>(), hscale(h), h->n, v0, n0, out, ld, nrhs, h->st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1524,119 +1558,160 @@ hsolve_status pcg_impl(hsolve_handle* h, double tol, int maxit, const double* b,
   return HSOLVE_OK;
 }
 
-// Right-preconditioned flexible GMRES(restart) with CGS2, one right-hand side
-// at a time.
-hsolve_status fgmres_one(hsolve_handle* h, double tol, int maxit, const double* b, double* x,
-                         int restart, int* iters, double* relres) {
+// Right-preconditioned flexible GMRES(restart) with CGS2 for a block of
+// right-hand sides at once: each column has its own Krylov space, Hessenberg
+// matrix and Givens rotations (host), but every preconditioner application,
+// SpMV and orthogonalisation runs on the whole n x nrhs block.  A column that
+// meets the tolerance stops contributing at that step of the cycle (its
+// solution update uses the steps up to it); the others continue.
+hsolve_status fgmres_batch(hsolve_handle* h, double tol, int maxit, const double* b, double* x,
+                           int nrhs, int64_t ldx, int restart, int* iters, double* relres) {
   const int64_t n = h->n;
   const int R = restart;
-  h->kry.ensure(sizeof(double) * ((size_t)(2 * R + 3) * n + 4 * (size_t)R + 256));
-  double* V = h->kry.as<double>();          // n x (R+1)
-  double* Z = V + (int64_t)(R + 1) * n;     // n x R
-  double* w = Z + (int64_t)R * n;           // n
-  double* coef = w + n;                     // R+1
-  std::vector<double> tmp;
-  dots_host(h, b, b, n, 1, tmp);
-  const double nb = std::sqrt(tmp[0]);
-  HS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, h->st));
-  if (nb == 0.0) {
-    *iters = 0;
-    *relres = 0;
-    return HSOLVE_OK;
-  }
+  const int64_t bs = n * (int64_t)nrhs;
+  h->kry.ensure(sizeof(double) * ((size_t)(2 * R + 2) * bs + 8 * (size_t)(R + 2) * nrhs + 256));
+  double* V = h->kry.as<double>();          // R+1 blocks
+  double* Z = V + (int64_t)(R + 1) * bs;    // R blocks
+  double* w = Z + (int64_t)R * bs;          // one block
+  double* coef = w + bs;                    // (R+2) * nrhs coefficients
+  const int kDotBlocks = 256;
+  auto block_dots = [&](int nv, const double* Vb, const double* wb, std::vector<double>& out) {
+    const int ncol = nv * nrhs;
+    h->dots.ensure(sizeof(double) * (size_t)(ncol + 64) * (kDotBlocks + 1));
+    double* d = h->dots.as<double>();
+    block_multi_dot(n, nv, nrhs, Vb, wb, d, h->st);
+    out.resize(ncol);
+    h->pin_small.ensure(sizeof(double) * (size_t)(ncol + 64) * 4);
+    HS_CUDA(cudaMemcpyAsync(h->pin_small.p, d + (int64_t)ncol * kDotBlocks, sizeof(double) * ncol,
+                            cudaMemcpyDeviceToHost, h->st));
+    HS_CUDA(cudaStreamSynchronize(h->st));
+    std::memcpy(out.data(), h->pin_small.p, sizeof(double) * ncol);
+  };
+  std::vector<double> nb2;
+  dots_host(h, b, b, ldx, nrhs, nb2);
+  std::vector<double> nb(nrhs), res(nrhs, 0.0);
+  for (int c = 0; c < nrhs; c++) nb[c] = std::sqrt(nb2[c]);
+  for (int c = 0; c < nrhs; c++) HS_CUDA(cudaMemsetAsync(x + c * ldx, 0, sizeof(double) * n, h->st));
+  std::vector<int> its(nrhs, 0);
+  std::vector<char> active(nrhs, 0);
+  std::vector<double> ones(nrhs, 1.0), mones(nrhs, -1.0), zeros(nrhs, 0.0);
   int total = 0;
-  double res = 1.0;
-  std::vector<double> one{1.0}, mone{-1.0};
-  while (total < maxit) {
-    // r = b - A x into V[:,0]
-    spmv_csr(n, h->d_rowptr.as<int64_t>(), h->d_col.as<int>(), h->d_val.as<double>(), x, n, w, n,
-             1, h->st);
-    HS_CUDA(cudaMemcpyAsync(V, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-    upload_coefs(h, one, coef);
-    upload_coefs(h, mone, coef + 1);
-    axpby_cols(n, 1, coef + 1, w, n, coef, V, n, h->st);  // V0 = -w + V0
-    dots_host(h, V, V, n, 1, tmp);
-    double beta = std::sqrt(tmp[0]);
-    res = beta / nb;
-    if (res <= tol) break;
-    std::vector<double> sc{1.0 / beta}, zero{0.0};
+  auto residual = [&]() {  // V_0 = b - A x, res = ||V_0|| / ||b||
+    spmv_csr(n, h->d_rowptr.as<int64_t>(), h->d_col.as<int>(), h->d_val.as<double>(), x, ldx, w,
+             n, nrhs, h->st);
+    for (int c = 0; c < nrhs; c++)
+      HS_CUDA(cudaMemcpyAsync(V + c * n, b + c * ldx, sizeof(double) * n,
+                              cudaMemcpyDeviceToDevice, h->st));
+    upload_coefs(h, ones, coef);
+    upload_coefs(h, mones, coef + nrhs);
+    axpby_cols(n, nrhs, coef + nrhs, w, n, coef, V, n, h->st);  // V0 = -w + V0
+    std::vector<double> r2;
+    dots_host(h, V, V, n, nrhs, r2);
+    std::vector<double> beta(nrhs);
+    for (int c = 0; c < nrhs; c++) {
+      beta[c] = std::sqrt(r2[c]);
+      res[c] = nb[c] > 0 ? beta[c] / nb[c] : 0.0;
+    }
+    return beta;
+  };
+  while (true) {
+    std::vector<double> beta = residual();
+    bool any = false;
+    for (int c = 0; c < nrhs; c++) {
+      active[c] = res[c] > tol;
+      any |= active[c] != 0;
+    }
+    if (!any || total >= maxit) break;
+    // V_0[:, c] /= beta_c (inactive columns become zero)
+    std::vector<double> sc(nrhs);
+    for (int c = 0; c < nrhs; c++) sc[c] = active[c] ? 1.0 / beta[c] : 0.0;
     upload_coefs(h, sc, coef);
-    upload_coefs(h, zero, coef + 1);
-    axpby_cols(n, 1, coef, V, n, coef + 1, V, n, h->st);
-    std::vector<std::vector<double>> H(R + 1, std::vector<double>(R, 0.0));
-    std::vector<double> cs(R), sn(R), g(R + 1, 0.0);
-    g[0] = beta;
-    int jdone = 0;
+    upload_coefs(h, zeros, coef + nrhs);
+    axpby_cols(n, nrhs, coef, V, n, coef + nrhs, V, n, h->st);
+    // per column: Hessenberg (column-major by step), rotations, g
+    std::vector<std::vector<double>> H(nrhs, std::vector<double>((size_t)(R + 1) * R, 0.0));
+    std::vector<std::vector<double>> cs(nrhs, std::vector<double>(R)),
+        sn(nrhs, std::vector<double>(R)), g(nrhs, std::vector<double>(R + 1, 0.0));
+    std::vector<int> jdone(nrhs, 0);
+    std::vector<char> open(active);  // still iterating in this cycle
+    for (int c = 0; c < nrhs; c++) g[c][0] = beta[c];
     for (int j = 0; j < R; j++) {
-      apply_any(h, V + (int64_t)j * n, Z + (int64_t)j * n, 1, n);
+      apply_any(h, V + j * bs, Z + j * bs, nrhs, n);
       spmv_csr(n, h->d_rowptr.as<int64_t>(), h->d_col.as<int>(), h->d_val.as<double>(),
-               Z + (int64_t)j * n, n, w, n, 1, h->st);
-      std::vector<double> hcol(j + 1, 0.0);
+               Z + j * bs, n, w, n, nrhs, h->st);
+      std::vector<double> hcol((size_t)(j + 1) * nrhs, 0.0);
       for (int pass = 0; pass < 2; pass++) {
-        h->dots.ensure(sizeof(double) * (size_t)(R + 64) * 257);
-        double* d = h->dots.as<double>();
-        multi_dot(n, j + 1, V, n, w, d, h->st);
-        std::vector<double> hh(j + 1);
-        h->pin_small.ensure(sizeof(double) * (R + 64) * 4);
-        HS_CUDA(cudaMemcpyAsync(h->pin_small.p, d + (int64_t)(j + 1) * 256,
-                                sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, h->st));
-        HS_CUDA(cudaStreamSynchronize(h->st));
-        std::memcpy(hh.data(), h->pin_small.p, sizeof(double) * (j + 1));
+        std::vector<double> hh;
+        block_dots(j + 1, V, w, hh);
         upload_coefs(h, hh, coef);
-        multi_axpy(n, j + 1, V, n, coef, -1.0, w, h->st);
-        for (int i = 0; i <= j; i++) hcol[i] += hh[i];
+        block_multi_axpy(n, j + 1, nrhs, V, coef, -1.0, w, n, h->st);
+        for (size_t q = 0; q < hh.size(); q++) hcol[q] += hh[q];
       }
-      dots_host(h, w, w, n, 1, tmp);
-      double hn = std::sqrt(tmp[0]);
-      for (int i = 0; i <= j; i++) H[i][j] = hcol[i];
-      H[j + 1][j] = hn;
-      if (hn > 0) {
-        std::vector<double> sc2{1.0 / hn}, z2{0.0};
-        upload_coefs(h, sc2, coef);
-        upload_coefs(h, z2, coef + 1);
-        HS_CUDA(cudaMemcpyAsync(V + (int64_t)(j + 1) * n, w, sizeof(double) * n,
-                                cudaMemcpyDeviceToDevice, h->st));
-        axpby_cols(n, 1, coef, V + (int64_t)(j + 1) * n, n, coef + 1, V + (int64_t)(j + 1) * n, n,
-                   h->st);
+      std::vector<double> w2;
+      dots_host(h, w, w, n, nrhs, w2);
+      std::vector<double> inv(nrhs);
+      for (int c = 0; c < nrhs; c++) {
+        const double hn = std::sqrt(w2[c]);
+        inv[c] = (open[c] && hn > 0) ? 1.0 / hn : 0.0;
+        if (!open[c]) continue;
+        std::vector<double>& Hc = H[c];
+        double* col = Hc.data() + (size_t)j * (R + 1);
+        for (int i = 0; i <= j; i++) col[i] = hcol[(size_t)i * nrhs + c];
+        col[j + 1] = hn;
+        for (int i = 0; i < j; i++) {
+          const double t = cs[c][i] * col[i] + sn[c][i] * col[i + 1];
+          col[i + 1] = -sn[c][i] * col[i] + cs[c][i] * col[i + 1];
+          col[i] = t;
+        }
+        const double den = std::hypot(col[j], col[j + 1]);
+        cs[c][j] = den > 0 ? col[j] / den : 1.0;
+        sn[c][j] = den > 0 ? col[j + 1] / den : 0.0;
+        col[j] = den;
+        col[j + 1] = 0;
+        g[c][j + 1] = -sn[c][j] * g[c][j];
+        g[c][j] = cs[c][j] * g[c][j];
+        jdone[c] = j + 1;
+        its[c]++;
+        if (std::fabs(g[c][j + 1]) <= tol * nb[c] || den == 0.0) open[c] = 0;
       }
-      for (int i = 0; i < j; i++) {
-        double t = cs[i] * H[i][j] + sn[i] * H[i + 1][j];
-        H[i + 1][j] = -sn[i] * H[i][j] + cs[i] * H[i + 1][j];
-        H[i][j] = t;
-      }
-      double den = std::hypot(H[j][j], H[j + 1][j]);
-      cs[j] = den > 0 ? H[j][j] / den : 1.0;
-      sn[j] = den > 0 ? H[j + 1][j] / den : 0.0;
-      H[j][j] = den;
-      H[j + 1][j] = 0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
+      // V_{j+1} = w / ||w|| (zero for columns no longer iterating)
+      upload_coefs(h, inv, coef);
+      upload_coefs(h, zeros, coef + nrhs);
+      axpby_cols(n, nrhs, coef, w, n, coef + nrhs, V + (j + 1) * bs, n, h->st);
       total++;
-      jdone = j + 1;
-      if (std::fabs(g[j + 1]) <= tol * nb || total >= maxit) break;
+      bool still = false;
+      for (int c = 0; c < nrhs; c++) still |= open[c] != 0;
+      if (!still || total >= maxit) break;
     }
-    // y = H^{-1} g, x += Z y
-    std::vector<double> y(jdone);
-    for (int i = jdone - 1; i >= 0; i--) {
-      double s = g[i];
-      for (int l = i + 1; l < jdone; l++) s -= H[i][l] * y[l];
-      y[i] = s / H[i][i];
+    // y_c = H_c^{-1} g_c over its jdone_c steps; x += Z y
+    int jmax = 0;
+    for (int c = 0; c < nrhs; c++) jmax = std::max(jmax, jdone[c]);
+    if (jmax == 0) break;
+    std::vector<double> Y((size_t)jmax * nrhs, 0.0);
+    for (int c = 0; c < nrhs; c++) {
+      const int jd = jdone[c];
+      const std::vector<double>& Hc = H[c];
+      std::vector<double> y(jd);
+      for (int i = jd - 1; i >= 0; i--) {
+        double t = g[c][i];
+        for (int l = i + 1; l < jd; l++) t -= Hc[(size_t)l * (R + 1) + i] * y[l];
+        const double d = Hc[(size_t)i * (R + 1) + i];
+        y[i] = d != 0.0 ? t / d : 0.0;
+      }
+      for (int i = 0; i < jd; i++) Y[(size_t)i * nrhs + c] = y[i];
     }
-    upload_coefs(h, y, coef);
-    multi_axpy(n, jdone, Z, n, coef, 1.0, x, h->st);
+    upload_coefs(h, Y, coef);
+    block_multi_axpy(n, jmax, nrhs, Z, coef, 1.0, x, ldx, h->st);
   }
-  // final true residual
-  spmv_csr(n, h->d_rowptr.as<int64_t>(), h->d_col.as<int>(), h->d_val.as<double>(), x, n, w, n, 1,
-           h->st);
-  HS_CUDA(cudaMemcpyAsync(V, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-  upload_coefs(h, one, coef);
-  upload_coefs(h, mone, coef + 1);
-  axpby_cols(n, 1, coef + 1, w, n, coef, V, n, h->st);
-  dots_host(h, V, V, n, 1, tmp);
-  res = std::sqrt(tmp[0]) / nb;
-  *iters = total;
-  *relres = res;
-  return res <= tol ? HSOLVE_OK : HSOLVE_ERR_NO_CONVERGENCE;
+  int itmax = 0;
+  double worst = 0;
+  for (int c = 0; c < nrhs; c++) {
+    itmax = std::max(itmax, its[c]);
+    worst = std::max(worst, res[c]);
+  }
+  *iters = itmax;
+  *relres = worst;
+  return worst <= tol ? HSOLVE_OK : HSOLVE_ERR_NO_CONVERGENCE;
 }
 
 }  // namespace
@@ -1821,19 +1896,31 @@ hsolve_status hsolve_factor(hsolve_handle* h, double eps, hsolve_precision prec)
 }
 
 hsolve_status hsolve_factor_forced(hsolve_handle* h, hsolve_precision prec, const int32_t* ranks,
-                                   const int32_t* counts, int32_t nlevels) {
+                                   const int32_t* counts, int32_t nlevels,
+                                   const int32_t* pivots) {
   if (!h || !ranks || !counts || nlevels < 1) return HSOLVE_ERR_ARG;
   h->forced.assign(nlevels, {});
-  int64_t o = 0;
+  h->forced_piv.clear();
+  int64_t o = 0, po = 0;
   for (int l = 0; l < nlevels; l++) {
     if (counts[l] < 0) return HSOLVE_ERR_ARG;
     h->forced[l].assign(ranks + o, ranks + o + counts[l]);
     o += counts[l];
+    if (pivots) {
+      int64_t np = 0;
+      for (int32_t k : h->forced[l]) {
+        if (k < 0) return HSOLVE_ERR_ARG;
+        np += k;
+      }
+      h->forced_piv.emplace_back(pivots + po, pivots + po + np);
+      po += np;
+    }
   }
   h->force_ranks = true;
   const hsolve_status st = hsolve_factor(h, 0.0, prec);
   h->force_ranks = false;
   h->forced.clear();
+  h->forced_piv.clear();
   return st;
 }
 
@@ -1928,6 +2015,34 @@ hsolve_status hsolve_tc_gemm(int mode, int M, int N, int K, const float* A, int6
   return rc;
 }
 
+hsolve_status hsolve_wait_selftest(int kind, int64_t limit_cycles, void* stream) {
+  if (kind != 0 || limit_cycles < 0) return HSOLVE_ERR_ARG;
+  cudaGetLastError();
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int* buf = nullptr;  // [0] error word
+  {
+    std::lock_guard<std::mutex> lk(device_mutex());
+    if (cudaMalloc(&buf, 8 * sizeof(int)) != cudaSuccess) return HSOLVE_ERR_OOM;
+  }
+  int e = 0;
+  hsolve_status rc = HSOLVE_OK;
+  if (cudaMemsetAsync(buf, 0, 8 * sizeof(int), st) != cudaSuccess) rc = HSOLVE_ERR_CUDA;
+  if (rc == HSOLVE_OK) {
+    mbar_wait_probe(limit_cycles, buf, st);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&e, buf, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = HSOLVE_ERR_CUDA;
+    else
+      rc = (hsolve_status)e;
+  }
+  {
+    std::lock_guard<std::mutex> lk(device_mutex());
+    cudaFree(buf);
+  }
+  return rc;
+}
+
 hsolve_status hsolve_solve(hsolve_handle* h, hsolve_krylov krylov, double tol, int maxit,
                            const double* b, double* x, int nrhs, int64_t ld,
                            hsolve_solve_info* info) {
@@ -1950,15 +2065,7 @@ hsolve_status hsolve_solve(hsolve_handle* h, hsolve_krylov krylov, double tol, i
       it = tmp.iterations;
       rr = tmp.rel_residual;
     } else {
-      for (int c = 0; c < nrhs; c++) {
-        int i1 = 0;
-        double r1 = 0;
-        hsolve_status s1 = fgmres_one(h, tol, maxit, b + c * ld, x + c * ld,
-                                      h->opts.gmres_restart, &i1, &r1);
-        if (s1 != HSOLVE_OK) st = s1;
-        it = std::max(it, i1);
-        rr = std::max(rr, r1);
-      }
+      st = fgmres_batch(h, tol, maxit, b, x, nrhs, ld, h->opts.gmres_restart, &it, &rr);
     }
     HS_CUDA(cudaEventRecord(e1, h->st));
     HS_CUDA(cudaEventSynchronize(e1));
@@ -2041,6 +2148,90 @@ hsolve_status hsolve_get_level(const hsolve_handle* h, int level, int32_t* nclu,
     if (sizes) sizes[i] = F.P.m[i];
     if (ranks) ranks[i] = i < (int)F.k.size() ? F.k[i] : 0;
     if (colour) colour[i] = F.P.colour[i];
+  }
+  return HSOLVE_OK;
+}
+
+hsolve_status hsolve_export_level(const hsolve_handle* hc, int level, hsolve_level_export* info,
+                                  hsolve_cluster_export* clusters, double* fac, int32_t* pivots,
+                                  int32_t* nbr_id, int32_t* nbr_w) {
+  hsolve_handle* h = const_cast<hsolve_handle*>(hc);
+  if (!h || !info) return HSOLVE_ERR_ARG;
+  if (!h->factored) return set_err(h, HSOLVE_ERR_STATE, "export before factor");
+  if (level < 0 || level >= (int)h->F.size()) return set_err(h, HSOLVE_ERR_ARG, "no such level");
+  const FLevel& F = *h->F[level];
+  const int nc = F.P.nclu;
+  const bool have = !F.hrecs.empty();  // false: a level that only merged into the top
+  const size_t esz = h->prec == HSOLVE_FP64 ? sizeof(double) : sizeof(float);
+  std::memset(info, 0, sizeof(*info));
+  info->nclu = nc;
+  info->dense_top = F.top ? 1 : 0;
+  info->symmetric = h->symmetric;
+  info->precision = h->prec;
+  info->fac_elems = have ? (int64_t)(F.fac.bytes / esz) : 0;
+  info->nbr_total = (int64_t)F.nb_id.size();
+  int64_t np = 0;
+  if (have)
+    for (int s = 0; s < nc; s++) np += F.hrecs[s].m > 0 ? F.hrecs[s].k : 0;
+  info->piv_total = np;
+  try {
+    if (clusters) {
+      int64_t po = 0;
+      for (int s = 0; s < nc; s++) {
+        hsolve_cluster_export& c = clusters[s];
+        std::memset(&c, 0, sizeof(c));
+        c.colour = s < (int)F.P.colour.size() ? F.P.colour[s] : 0;
+        c.T = c.TR = c.Y = c.XT = -1;
+        c.piv = po;
+        c.nb = have ? F.nb_ptr[s] : 0;
+        if (!have) continue;
+        const ApplyRec& r = F.hrecs[s];
+        c.m = r.m;
+        c.k = r.m > 0 ? r.k : 0;
+        c.nw = r.nw;
+        c.nnb = F.nb_ptr[s + 1] - F.nb_ptr[s];
+        c.npiv = c.k;
+        po += c.npiv;
+        if (r.m > 0 && r.k < r.m) {
+          c.T = r.T;
+          c.Y = r.nw > 0 ? r.Y : -1;
+          if (!r.sym) {
+            c.TR = r.TR;
+            c.XT = r.nw > 0 ? r.XT : -1;
+          }
+        }
+      }
+    }
+    if (fac && have && info->fac_elems > 0) {
+      std::vector<char> buf(F.fac.bytes);
+      HS_CUDA(cudaMemcpyAsync(buf.data(), F.fac.p, F.fac.bytes, cudaMemcpyDeviceToHost, h->st));
+      HS_CUDA(cudaStreamSynchronize(h->st));
+      if (esz == sizeof(double)) {
+        std::memcpy(fac, buf.data(), sizeof(double) * info->fac_elems);
+      } else {
+        const float* f = reinterpret_cast<const float*>(buf.data());
+        for (int64_t i = 0; i < info->fac_elems; i++) fac[i] = f[i];
+      }
+    }
+    if (pivots && have && np > 0) {
+      std::vector<int> all((size_t)std::max<int64_t>(F.P.voff[nc], 1));
+      HS_CUDA(cudaMemcpyAsync(all.data(), F.piv.p, sizeof(int) * F.P.voff[nc],
+                              cudaMemcpyDeviceToHost, h->st));
+      HS_CUDA(cudaStreamSynchronize(h->st));
+      int64_t po = 0;
+      for (int s = 0; s < nc; s++) {
+        const ApplyRec& r = F.hrecs[s];
+        if (r.m == 0) continue;
+        for (int j = 0; j < r.k; j++) pivots[po + j] = all[F.P.voff[s] + j];
+        po += r.k;
+      }
+    }
+    if (nbr_id)
+      for (size_t i = 0; i < F.nb_id.size(); i++) nbr_id[i] = F.nb_id[i];
+    if (nbr_w)
+      for (size_t i = 0; i < F.nb_w.size(); i++) nbr_w[i] = F.nb_w[i];
+  } catch (const Fail& f) {
+    return set_err(h, f.code, f.msg);
   }
   return HSOLVE_OK;
 }

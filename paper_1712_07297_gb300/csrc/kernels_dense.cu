@@ -331,7 +331,8 @@ __device__ double cta_sum_d(double v, double* red) {
 template <typename real, bool RowMajor>
 __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, double* orig,
                                   real* tau, bool pivot, double eps, int kmax, double floor,
-                                  double* red_d, int* red_i, real* vsh, real* rsign = nullptr) {
+                                  double* red_d, int* red_i, real* vsh, real* rsign = nullptr,
+                                  const int* fpiv = nullptr) {
   auto at = [&](int i, int q) -> real& {
     return RowMajor ? G[(int64_t)i * ldg + q] : G[i + (int64_t)q * ldg];
   };
@@ -359,14 +360,22 @@ __device__ int cta_householder_qr(int m, int c, real* G, int ldg, double* nrm2, 
       mx = cta_max_d(mx, red_d);
       if (mx == 0.0) break;
       int best = INT_MAX;
-      for (int t = j + threadIdx.x; t < c; t += blockDim.x)
-        if (nrm2[t] >= (1.0 - qr_tie_rtol<real>()) * mx) best = min(best, (int)orig[t]);
-      best = cta_min_i(best, red_i);
+      if (fpiv) {
+        // a given pivot order (forced-rank factorization) replaces the search
+        best = j < kmax ? fpiv[j] : INT_MAX;
+      } else {
+        for (int t = j + threadIdx.x; t < c; t += blockDim.x)
+          if (nrm2[t] >= (1.0 - qr_tie_rtol<real>()) * mx) best = min(best, (int)orig[t]);
+        best = cta_min_i(best, red_i);
+      }
+      if (threadIdx.x == 0) red_i[blockDim.x] = -1;
+      __syncthreads();
       for (int t = j + threadIdx.x; t < c; t += blockDim.x)
         if ((int)orig[t] == best) red_i[blockDim.x] = t;
       __syncthreads();
       q = red_i[blockDim.x];
       __syncthreads();
+      if (q < 0) break;  // the given pivot names no remaining column
       r = sqrt(nrm2[q]);
       if (j == 0) r11 = r;
       if (r <= floor) break;
@@ -644,8 +653,9 @@ template <typename real>
 __global__ void __launch_bounds__(PrepThreads<real>::value)
 prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* __restrict__ fac,
             real* __restrict__ ws_all, double* __restrict__ wsd_all,
-            const Seg* __restrict__ segs, int* rank,
-            double eps, double noise_rtol, int sym, int max_rank, int smem_mats, int smem_m,
+            const Seg* __restrict__ segs, int* rank, int* __restrict__ piv_all,
+            const int* __restrict__ fpiv, double eps, double noise_rtol, int sym, int max_rank,
+            int smem_mats, int smem_m,
             DevError* err, int level, long long* dbg) {
   __shared__ double red_d[PrepThreads<real>::value];
   __shared__ int red_i[PrepThreads<real>::value + 1];
@@ -799,14 +809,20 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
     const int ldY = ysm ? (m | 1) : m;
     if (ysm) cta_copy<real>(m, tk.l, Ysrc, m, Yq, ldY);
     k = cta_householder_qr<real, false>(m, tk.l, Yq, ldY, nrm2, orig, tau, true, eps, kmax,
-                                        noise_rtol * s_amax, red_d, red_i, vsh, rsign);
+                                        noise_rtol * s_amax, red_d, red_i, vsh, rsign,
+                                        fpiv ? fpiv + tk.pv : nullptr);
     cta_copy<real>(m, k, Yq, ldY, W_G, m);
   } else if (ncol > 0) {
     k = cta_householder_qr<real, true>(m, ncol, W_G, ncol, nrm2, orig, tau, true, eps, kmax,
-                                       noise_rtol * s_amax, red_d, red_i, vsh, rsign);
+                                       noise_rtol * s_amax, red_d, red_i, vsh, rsign,
+                                       fpiv ? fpiv + tk.pv : nullptr);
   }
   __syncthreads();
   if (threadIdx.x == 0) rank[tk.s] = k;
+  // pivot order (the cluster kernel recorded its own): orig[j] is the
+  // compacted (or sketch) column chosen at step j
+  if (!qr_done)
+    for (int j = threadIdx.x; j < k; j += blockDim.x) piv_all[tk.pv + j] = (int)orig[j];
   mark(3);
   if (k == m) return;  // untouched: all unknowns coarse, E_s = I
   const int f = m - k;
@@ -945,7 +961,8 @@ prep_kernel(const PrepTask* __restrict__ tasks, real* __restrict__ arena, real* 
 
 template <typename real>
 void Launch<real>::prep(const PrepTask* tasks_dev, int ntask, real* arena, real* fac, real* ws,
-                        double* wsd, const Seg* segs, int* rank, double eps,
+                        double* wsd, const Seg* segs, int* rank, int* piv, const int* fpiv,
+                        double eps,
                         int sym, int max_rank, int maxm, DevError* err, int level,
                         long long* dbg, cudaStream_t st) {
   if (ntask <= 0) return;
@@ -971,7 +988,7 @@ void Launch<real>::prep(const PrepTask* tasks_dev, int ntask, real* arena, real*
   (void)limit_set;
   count_launch();
   prep_kernel<real><<<ntask, PrepThreads<real>::value, smem, st>>>(tasks_dev, arena, fac, ws, wsd, segs,
-                                                        rank, eps, noise_rtol, sym, max_rank, mats,
+                                                        rank, piv, fpiv, eps, noise_rtol, sym, max_rank, mats,
                                                         maxm, err, level, dbg);
 }
 

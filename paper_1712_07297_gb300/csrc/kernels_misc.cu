@@ -398,14 +398,15 @@ __global__ void spmv_kernel(int64_t n, const int64_t* __restrict__ rp, const int
 
 constexpr int kDotBlocks = 256;
 
-// partial[c * kDotBlocks + b] = sum over this block's rows of a[:,c] * b[:,c]
+// partial[c * kDotBlocks + b] = sum over this block's rows of
+// a[:,c] * b[:, c mod bmod]
 __global__ void dots_partial(int64_t n, const double* __restrict__ a, int64_t lda,
-                             const double* __restrict__ b, int64_t ldb, int ncol, int bcast,
+                             const double* __restrict__ b, int64_t ldb, int ncol, int bmod,
                              double* __restrict__ part) {
   __shared__ double red[256];
   for (int c = 0; c < ncol; c++) {
     const double* ac = a + c * lda;
-    const double* bc = b + (bcast ? 0 : c * ldb);
+    const double* bc = b + (int64_t)(c % bmod) * ldb;
     double s = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -433,14 +434,19 @@ __global__ void dots_final(const double* __restrict__ part, int ncol, double* __
   if (threadIdx.x == 0) out[c] = red[0];
 }
 
-__global__ void multi_axpy_kernel(int64_t n, int nv, const double* __restrict__ V, int64_t ldv,
-                                  const double* __restrict__ coef, double sign,
-                                  double* __restrict__ w) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+// w[:, c] += sign * sum_i coef[i * nrhs + c] V_i[:, c] for the nv blocks
+// V_i (n x nrhs, ld n, block stride n * nrhs)
+__global__ void block_multi_axpy_kernel(int64_t n, int nv, int nrhs, const double* __restrict__ V,
+                                        const double* __restrict__ coef, double sign,
+                                        double* __restrict__ w, int64_t ldw) {
+  const int64_t bs = n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < bs;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n;
+    const int c = (int)(e / n);
     double acc = 0;
-    for (int j = 0; j < nv; j++) acc += V[i + j * ldv] * coef[j];
-    w[i] += sign * acc;
+    for (int j = 0; j < nv; j++) acc += V[j * bs + e] * coef[j * nrhs + c];
+    w[i + c * ldw] += sign * acc;
   }
 }
 
@@ -590,23 +596,27 @@ void spmv_csr(int64_t n, const int64_t* rp, const int* ci, const double* v, cons
 void dots(int64_t n, const double* a, int64_t lda, const double* b, int64_t ldb, int nrhs,
           double* out, cudaStream_t st) {
   count_launch();
-  dots_partial<<<kDotBlocks, 256, 0, st>>>(n, a, lda, b, ldb, nrhs, 0, out);
+  dots_partial<<<kDotBlocks, 256, 0, st>>>(n, a, lda, b, ldb, nrhs, nrhs, out);
   count_launch();
   dots_final<<<nrhs, kDotBlocks, 0, st>>>(out, nrhs, out + (int64_t)nrhs * kDotBlocks);
 }
 
-void multi_dot(int64_t n, int nv, const double* V, int64_t ldv, const double* w, double* out,
-               cudaStream_t st) {
+void block_multi_dot(int64_t n, int nv, int nrhs, const double* V, const double* w,
+                     double* out, cudaStream_t st) {
+  // column q = i * nrhs + c of the nv blocks is V_i[:, c] (stride n); it
+  // meets w[:, c] = w[:, q mod nrhs]
+  const int ncol = nv * nrhs;
   count_launch();
-  dots_partial<<<kDotBlocks, 256, 0, st>>>(n, V, ldv, w, 0, nv, 1, out);
+  dots_partial<<<kDotBlocks, 256, 0, st>>>(n, V, n, w, n, ncol, nrhs, out);
   count_launch();
-  dots_final<<<nv, kDotBlocks, 0, st>>>(out, nv, out + (int64_t)nv * kDotBlocks);
+  dots_final<<<ncol, kDotBlocks, 0, st>>>(out, ncol, out + (int64_t)ncol * kDotBlocks);
 }
 
-void multi_axpy(int64_t n, int nv, const double* V, int64_t ldv, const double* coef, double sign,
-                double* w, cudaStream_t st) {
+void block_multi_axpy(int64_t n, int nv, int nrhs, const double* V, const double* coef,
+                      double sign, double* w, int64_t ldw, cudaStream_t st) {
   count_launch();
-  multi_axpy_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, nv, V, ldv, coef, sign, w);
+  block_multi_axpy_kernel<<<grid_for(n * nrhs, 256), 256, 0, st>>>(n, nv, nrhs, V, coef, sign,
+                                                                    w, ldw);
 }
 
 void axpby_cols(int64_t n, int nrhs, const double* alpha, const double* x, int64_t ldx,

@@ -92,8 +92,9 @@ template <typename real>
 __global__ void __launch_bounds__(kQrThreads)
 qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ arena,
                   real* __restrict__ ws_all, double* __restrict__ wsd_all,
-                  const Seg* __restrict__ segs, int* rank, const int* __restrict__ cnt,
-                  double eps, double noise_rtol, int max_rank, int ldsm, int ccmax) {
+                  const Seg* __restrict__ segs, int* rank, int* __restrict__ piv,
+                  const int* __restrict__ fpiv, const int* __restrict__ cnt, double eps,
+                  double noise_rtol, int max_rank, int ldsm, int ccmax) {
   cg::cluster_group cl = cg::this_cluster();
   const int CL = (int)cl.num_blocks();
   const int cr = (int)cl.block_rank();
@@ -207,10 +208,12 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
     const double M = s_M;
     if (M <= 0.0) break;
     // 2. lowest original index among the near-maximal columns: one key
-    //    (original index, local slot) per candidate, the smallest wins
+    //    (original index, local slot) per candidate, the smallest wins; a
+    //    given pivot order (fpiv) makes its column the only candidate
     unsigned long long key = ~0ull;
+    const int fq = fpiv ? fpiv[tk.pv + j] : -1;
     for (int t = threadIdx.x; t < nloc; t += blockDim.x)
-      if (nrm[t] >= (1.0 - tie_rtol<real>()) * M) {
+      if (fpiv ? (z0 + t == fq && nrm[t] >= 0.0) : (nrm[t] >= (1.0 - tie_rtol<real>()) * M)) {
         const unsigned long long kk = ((unsigned long long)oidx[t] << 32) | (unsigned)t;
         key = kk < key ? kk : key;
       }
@@ -239,6 +242,7 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
     __syncthreads();
     const int owner = s_owner;
     const double r = s_r;
+    if (!(r >= 0.0)) break;  // a given pivot that names no remaining column
     if (j == 0) r11 = r;
     if (r <= floor || (eps > 0.0 && r <= eps * r11) || j >= kmax) break;
     // 3. every CTA forms the reflector v = x - beta e1, beta = -sign(x0) ||x||
@@ -259,6 +263,9 @@ qr_cluster_kernel(const PrepTask* __restrict__ tasks, const real* __restrict__ a
       tau_g[j] = tj;
       rsign_g[j] = beta < 0.0 ? real(-1) : real(1);
       nrm[oloc] = -1.0;  // used: out of every later step
+      // the pivot as an index among the nonzero gathered columns: slot t of
+      // CTA cr holds nonzero column z0 + t
+      piv[tk.pv + j] = z0 + oloc;
     }
     __syncthreads();
     // 4. every CTA applies the reflector to its remaining columns and
@@ -380,8 +387,8 @@ size_t Launch<real>::qr_cluster_smem(int maxm, int maxc, int CL) {
 template <typename real>
 void Launch<real>::qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, int maxc, int CL,
                               const real* arena, real* ws, double* wsd, const Seg* segs,
-                              int* rank, const int* cnt, double eps, int max_rank,
-                              cudaStream_t st) {
+                              int* rank, int* piv, const int* fpiv, const int* cnt, double eps,
+                              int max_rank, cudaStream_t st) {
   if (ntask <= 0) return;
   const double noise_rtol = sizeof(real) == 8 ? 1e-14 : 1e-6;
   const size_t smem = qr_cluster_smem(maxm, maxc, CL);
@@ -413,7 +420,7 @@ void Launch<real>::qr_cluster(const PrepTask* tasks_dev, int ntask, int maxm, in
     cfg.numAttrs = 1;
     count_launch();
     cudaLaunchKernelEx(&cfg, qr_cluster_kernel<real>, tasks_dev + t0, arena, ws, wsd, segs, rank,
-                       cnt + t0, eps, noise_rtol, max_rank, (maxm + 1) | 1, cc);
+                       piv, fpiv, cnt + t0, eps, noise_rtol, max_rank, (maxm + 1) | 1, cc);
   }
 }
 

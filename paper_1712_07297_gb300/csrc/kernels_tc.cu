@@ -63,8 +63,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// Wait for the phase with the given parity; false after about a second.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase with the given parity; false after `limit` SM clocks
+// (about a second by default).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = 2000000000ll) {
   const long long t0 = clock64();
   while (true) {
     uint32_t done;
@@ -75,7 +77,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > 2000000000ll) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -761,6 +763,22 @@ void dense_top_tc(float* A, int64_t lda, int n, float* X, float* W, DevError* er
                   cudaStream_t st) {
   if (n <= 0) return;
   top_rec(A, lda, X, n, n, W, err, level, st);
+}
+
+// Diagnostic of the bounded mbarrier wait: one thread waits, with the given
+// limit, on a barrier nothing arrives at; the expired wait records
+// HSOLVE_ERR_TIMEOUT.  No asynchronous copy or tensor-core operation is in
+// flight, so the early return leaves nothing behind.
+__global__ void mbar_wait_probe_kernel(long long limit, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit)) *err = (int)HSOLVE_ERR_TIMEOUT;
+}
+
+void mbar_wait_probe(long long limit, int* err, cudaStream_t st) {
+  count_launch();
+  mbar_wait_probe_kernel<<<1, 32, 0, st>>>(limit, err);
 }
 
 }  // namespace hs

@@ -57,6 +57,18 @@ class Stats(C.Structure):
                 ("qr_flops", C.c_double)]
 
 
+class ClusterExport(C.Structure):
+    _fields_ = [("m", C.c_int32), ("k", C.c_int32), ("nw", C.c_int32), ("nnb", C.c_int32),
+                ("colour", C.c_int32), ("npiv", C.c_int32), ("T", C.c_int64), ("TR", C.c_int64),
+                ("Y", C.c_int64), ("XT", C.c_int64), ("piv", C.c_int64), ("nb", C.c_int64)]
+
+
+class LevelExport(C.Structure):
+    _fields_ = [("nclu", C.c_int32), ("dense_top", C.c_int32), ("symmetric", C.c_int32),
+                ("precision", C.c_int32), ("fac_elems", C.c_int64), ("piv_total", C.c_int64),
+                ("nbr_total", C.c_int64)]
+
+
 class PhaseTime(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("ms", C.c_double), ("launches", C.c_int32)]
 
@@ -66,7 +78,8 @@ EXPORTS = {
     "hsolve_analyze": (C.c_int, [C.POINTER(Csr), C.c_void_p, C.c_int, C.POINTER(Opts), C.c_void_p,
                                  C.POINTER(C.c_void_p)]),
     "hsolve_factor": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
-    "hsolve_factor_forced": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int32]),
+    "hsolve_factor_forced": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int32,
+                                       C.c_void_p]),
     "hsolve_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int64]),
     "hsolve_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int64]),
     "hsolve_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
@@ -78,11 +91,14 @@ EXPORTS = {
     "hsolve_get_level": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_int32]),
     "hsolve_get_perm": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "hsolve_export_level": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(LevelExport), C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hsolve_get_phase_times": (C.c_int, [C.c_void_p, C.POINTER(PhaseTime), C.c_int32,
                                          C.POINTER(C.c_int32)]),
     "hsolve_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "hsolve_last_error": (C.c_char_p, [C.c_void_p]),
     "hsolve_destroy": (None, [C.c_void_p]),
+    "hsolve_wait_selftest": (C.c_int, [C.c_int, C.c_int64, C.c_void_p]),
     "hsolve_tc_gemm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64,
                                  C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
                                  C.c_int64, C.c_float, C.c_float, C.c_int, C.c_void_p]),
@@ -218,16 +234,27 @@ class Solver:
         p = PRECISION[precision] if isinstance(precision, str) else int(precision)
         _check(load().hsolve_factor(self.h, float(eps), p), self.h)
 
-    def factor_forced(self, precision, ranks_per_level):
+    def factor_forced(self, precision, ranks_per_level, pivots_per_level=None):
         """Factor with every cluster's rank fixed (hsolve_factor_forced):
-        ranks_per_level[l] = the ranks of level l's clusters."""
-        import numpy as np
+        ranks_per_level[l] = the ranks of level l's clusters; optionally
+        pivots_per_level[l][s] = cluster s's pivot order (ranks_per_level[l][s]
+        column indices)."""
         p = PRECISION[precision] if isinstance(precision, str) else int(precision)
         counts = np.array([len(r) for r in ranks_per_level], dtype=np.int32)
         flat = np.ascontiguousarray(np.concatenate([np.asarray(r, dtype=np.int32)
                                                     for r in ranks_per_level]))
+        pv = None
+        if pivots_per_level is not None:
+            parts = [np.asarray(q, dtype=np.int32).ravel()
+                     for lv in pivots_per_level for q in lv]
+            for lv, rk in zip(pivots_per_level, ranks_per_level):
+                if [len(q) for q in lv] != [int(k) for k in rk]:
+                    raise ValueError("pivot lists must have ranks[s] entries")
+            pv = np.ascontiguousarray(np.concatenate(parts) if parts else
+                                      np.zeros(1, dtype=np.int32))
         _check(load().hsolve_factor_forced(self.h, p, flat.ctypes.data, counts.ctypes.data,
-                                           len(counts)), self.h)
+                                           len(counts), None if pv is None else pv.ctypes.data),
+               self.h)
 
     def apply(self, rhs, out=None):
         """out = M^{-1} rhs on the device (torch float64 CUDA tensors)."""
@@ -302,6 +329,42 @@ class Solver:
                                     ranks.ctypes.data, colour.ctypes.data, nc.value), self.h)
         return sizes, ranks, colour
 
+    def export_level(self, level: int, blocks: bool = True) -> dict:
+        """The stored operators of one level (hsolve_export_level): a dict with
+        the level's flags and, per cluster, m, k, nw, colour, pivots,
+        neighbours (id, width) and (blocks=True) the blocks T', T'_R^T, Y, X^T
+        as float64 arrays (None where the factorization keeps none)."""
+        lib = load()
+        info = LevelExport()
+        _check(lib.hsolve_export_level(self.h, level, C.byref(info), None, None, None, None,
+                                       None), self.h)
+        nc = info.nclu
+        recs = (ClusterExport * max(nc, 1))()
+        fac = np.zeros(max(info.fac_elems, 1) if blocks else 1, dtype=np.float64)
+        piv = np.zeros(max(info.piv_total, 1), dtype=np.int32)
+        nid = np.zeros(max(info.nbr_total, 1), dtype=np.int32)
+        nw = np.zeros(max(info.nbr_total, 1), dtype=np.int32)
+        _check(lib.hsolve_export_level(self.h, level, C.byref(info), recs,
+                                       fac.ctypes.data if blocks else None, piv.ctypes.data,
+                                       nid.ctypes.data, nw.ctypes.data), self.h)
+
+        def blk(off, rows, cols):
+            if not blocks or off < 0 or rows == 0 or cols == 0:
+                return None
+            return fac[off:off + rows * cols].reshape(cols, rows).T.copy()
+
+        out = []
+        for s in range(nc):
+            r = recs[s]
+            m, k = r.m, r.k
+            out.append(dict(
+                m=m, k=k, nw=r.nw, colour=r.colour, piv=piv[r.piv:r.piv + r.npiv].copy(),
+                nbrs=list(zip(nid[r.nb:r.nb + r.nnb].tolist(), nw[r.nb:r.nb + r.nnb].tolist())),
+                T=blk(r.T, m, m), TRt=blk(r.TR, m, m), Y=blk(r.Y, m, r.nw),
+                XT=blk(r.XT, m, r.nw)))
+        return dict(nclu=nc, dense_top=bool(info.dense_top), symmetric=bool(info.symmetric),
+                    precision=info.precision, clusters=out)
+
     def perm(self) -> np.ndarray:
         p = np.zeros(self.n, dtype=np.int64)
         _check(load().hsolve_get_perm(self.h, p.ctypes.data), self.h)
@@ -318,6 +381,13 @@ class Solver:
         arr = (PhaseTime * max(cnt.value, 1))()
         _check(lib.hsolve_get_phase_times(self.h, arr, cnt.value, C.byref(cnt)), self.h)
         return {arr[i].name.decode(): (arr[i].ms, arr[i].launches) for i in range(cnt.value)}
+
+
+def wait_selftest(kind: str, limit_cycles: int) -> int:
+    """Run one bounded device wait that nothing signals (hsolve_wait_selftest):
+    kind "mbarrier" (the tensor-core kernels' wait); returns the status code
+    (HSOLVE_ERR_TIMEOUT = -8 when it gave up)."""
+    return load().hsolve_wait_selftest({"mbarrier": 0}[kind], int(limit_cycles), None)
 
 
 def tc_gemm(mode, A, B, C_, alpha=1.0, beta=0.0, lower=False, stream=None):
