@@ -1,19 +1,22 @@
 """Benchmark: factor + solve latency of the hierarchical solver on one GB300.
 
-One step = hsolve_factor (all levels of Alg. 1) + hsolve_solve (float64 PCG
-preconditioned by Alg. 2) of the 3D 7-point Poisson problem on a 64^3 grid
-(N = 262,144), clusters of 128 unknowns, eps = 1e-2, one right-hand side with
-entries uniform in [-1, 1], to a relative residual of 1e-10.  Analysis and the
-matrix upload are outside the timed region.
+One step = hsolve_factor (all levels of Alg. 1) + hsolve_solve (float64
+Krylov method preconditioned by Alg. 2) of the default workload, the largest
+single-GPU one: the 3D 7-point Poisson problem on a 128^3 grid (N =
+2,097,152), clusters of 128 unknowns, eps = 1e-2, eight right-hand sides with
+entries uniform in [-1, 1], flexible GMRES in float64 to a relative residual
+of 1e-10.  Analysis and the matrix upload are outside the timed region.
 
 The JSON line reports the mixed-precision path (`value`: float32
-factorization and sweeps inside float64 PCG) and the plain float64 path
-(`fp64`), p50/p99 over the steps, an end-to-end figure through the host-buffer
-entry point, the roofline of the dominant kernel and of the substitution
-sweeps, the CPU oracle baseline and the SM clocks seen while timing.
+factorization and sweeps inside the float64 Krylov method) and the plain
+float64 path (`fp64`), p50/p99 over the steps, an end-to-end figure through
+the host-buffer entry point, the roofline of the dominant kernel and of the
+substitution sweeps (algorithmic work from the factorization's own ranks and
+sizes, peaks from GEMM probes run here), the CPU oracle baseline and the SM
+clocks seen while timing.
 
 `--impl reference` times the CPU oracle (float64 numpy restatement of the
-method) on the host cores instead.
+method) on the host cores instead, on a bounded sample of the workload.
 
 Multi-GPU: the method runs on one GPU with no sharding; under torchrun every
 rank runs an independent replica and rank 0 reports the slowest rank.
@@ -34,7 +37,32 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "factor+solve ms to 1e-10 rel. residual, mixed vs FP64 on GPU; p50/p99 latency"
-WORKLOAD = "poisson3d_64"
+WORKLOAD = "poisson3d_128"
+# what each workload is, for config.workload
+DESCRIBE = {
+    "poisson3d_128": "3D 7-point Poisson 128^3 (N=2097152), clusters of 128, eps=1e-2, "
+                     "8 RHS U[-1,1], FGMRES(50) to 1e-10",
+    "poisson3d_64": "3D 7-point Poisson 64^3 (N=262144), clusters of 128, eps=1e-2, "
+                    "1 RHS U[-1,1], PCG to 1e-10",
+    "poisson3d_32": "3D 7-point Poisson 32^3 (N=32768), clusters of 128, eps=1e-2, "
+                    "1 RHS U[-1,1], PCG to 1e-10",
+    "poisson2d_64": "2D 5-point Poisson 64^2 (N=4096), clusters of 64, eps=1e-3, "
+                    "1 RHS U[-1,1], PCG to 1e-10",
+    "vcdiff3d_96": "3D variable-coefficient diffusion 96^3 (N=884736), 10^U(-3,3) cells, "
+                   "S A S equilibrated, clusters of 128, eps=1e-2, 1 RHS, PCG to 1e-10",
+    "convdiff3d_64": "3D convection-diffusion 64^3 (N=262144), Pe=10, clusters of 128, "
+                     "eps=1e-2, 1 RHS, FGMRES(50) to 1e-10",
+    "helmholtz3d_64": "3D Helmholtz -Lap-k^2 64^3 (N=262144), 32 points per wavelength, "
+                      "clusters of 128, eps=1e-2, 1 RHS, FGMRES(50) to 1e-3",
+}
+# the bounded sample of each workload the CPU oracle is timed on: the same
+# family, leaf, eps, Krylov method, tolerance and right-hand sides on a
+# smaller grid; its time is scaled by the ratio of unknowns (the method's
+# O(N) cost, Sec. 4)
+SAMPLE_SHAPE = {"poisson3d_128": (32, 32, 32), "poisson3d_64": (32, 32, 32),
+                "poisson3d_32": (16, 16, 16), "poisson2d_64": (32, 32),
+                "vcdiff3d_96": (24, 24, 24), "convdiff3d_64": (24, 24, 24),
+                "helmholtz3d_64": (24, 24, 24)}
 
 
 def _peaks():
@@ -52,6 +80,81 @@ def alu_peak_tflops(dtype: str, sm_mhz: float) -> float:
     per SM, the rate behind the 1.25 TFLOP/s nominal figure)."""
     fp32 = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     return fp32 if dtype == "f32" else fp32 / 64.0
+
+
+def gemm_probes():
+    """Measured GEMM rates on this GPU (cuBLAS through torch, best of 5, CUDA
+    events): float64 (DGEMM 4096^3), float32 without tensor cores (SGEMM
+    8192^3, TF32 off: the FP32 SIMT rate the per-cluster kernels are bound
+    by) and TF32 (SGEMM 8192^3, TF32 on)."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, n, dt, tf32 in (("fp64", 4096, torch.float64, False),
+                                  ("fp32_simt", 8192, torch.float32, False),
+                                  ("tf32", 8192, torch.float32, True)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            c = torch.empty(n, n, dtype=dt, device="cuda")
+            torch.matmul(a, b, out=c)
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[name] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        torch.cuda.empty_cache()
+    out["how"] = ("cuBLAS via torch.matmul, best of 5 (CUDA events): DGEMM 4096^3, "
+                  "SGEMM 8192^3 with TF32 off (fp32_simt) and on (tf32); TFLOP/s")
+    return out
+
+
+def algorithmic_work(s, stats, nrhs):
+    """The algorithmic work of the current factorization from its own ranks and
+    sizes (hsolve_export_level records), per the formulas of the method's
+    cost model: per processed cluster with k < m (f = m - k, nw = the
+    neighbours' widths, dense: the structural support of the neighbour blocks
+    is not tracked) --
+      prep (factor of A_ss, complement, sparsification): 2/3 m^3 + 6 m^2 k + 2 m^3
+      Schur update (Eq. elim):                            2 f nw^2
+      sweeps (Alg. 2, both directions): operators 2 (m^2 + f nw) words read
+        (T' and B_R in the symmetric case; T', T'_R, B_L, B_R once each in
+        the general one), vectors 2 (2 m + 2 nw) words per right-hand side;
+      the dense top: 2 n^2 words of its inverse factor, read twice,
+    plus the pivoted QR's 4 m c k (library counter, c = nonzero fill columns)."""
+    word = 8 if stats["precision"] == 0 else 4
+    prep = schur = 0.0
+    ops = vecs = 0
+    for lv in range(stats["levels"]):
+        ex = s.export_level(lv, blocks=False)
+        for c in ex["clusters"]:
+            m, k, nw = c["m"], c["k"], c["nw"]
+            if m == 0 or k >= m:
+                continue
+            f = m - k
+            if ex["dense_top"]:
+                ops += 2 * m * m
+                vecs += 4 * m
+                continue
+            prep += 2.0 / 3.0 * m ** 3 + 6.0 * m * m * k + 2.0 * m ** 3
+            schur += 2.0 * f * nw * nw
+            ops += 2 * (m * m + f * nw)
+            vecs += 2 * (2 * m + 2 * nw)
+    return {"prep_flops": prep, "schur_flops": schur, "qr_flops": stats["qr_flops"],
+            "gemm_flops": stats["gemm_flops"],
+            "apply_bytes": word * (ops + vecs * nrhs), "apply_operator_bytes": word * ops,
+            "apply_vector_bytes_per_rhs": word * vecs}
 
 
 class ClockSampler:
@@ -156,7 +259,8 @@ def run_gpu(args, rank, world):
     s = hsolve.Solver.from_problem(prob, leaf_size=leaf, symmetric=1 if prob.spd else 0,
                                    top_size=args.top_size, stream=stream,
                                    equilibrate=st.get("equilibrate", 0))
-    krylov = "pcg" if prob.spd else "gmres"
+    krylov = st["krylov"]
+    tol = st.get("tol", 1e-10)
     b_host = I.rhs(prob.n, nrhs, seed=st["rhs_seed"])
     b = torch.from_numpy(b_host).cuda()
     x = torch.empty_like(b)
@@ -164,7 +268,7 @@ def run_gpu(args, rank, world):
 
     def one_step(prec):
         s.factor(eps, prec)
-        _, info = s.solve(b, x, krylov=krylov, tol=1e-10, maxit=500)
+        _, info = s.solve(b, x, krylov=krylov, tol=tol, maxit=500)
         return info
 
     def timed_steps(prec, steps, warmup, phases):
@@ -202,7 +306,10 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    t64, i64 = timed_steps("fp64", args.steps, args.warmup, ph64)
+    # the float64 path is the comparison: fewer steps (each takes several
+    # times longer), still at least one untimed warm-up
+    fp64_steps = max(1, min(args.steps, args.fp64_steps))
+    t64, i64 = timed_steps("fp64", fp64_steps, max(1, min(args.warmup, 2)), ph64)
     st64 = s.stats()
     torch.cuda.synchronize()
 
@@ -212,7 +319,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.factor(eps, args.mixed)
-        xh, info = s.solve_host(b_host, krylov=krylov, tol=1e-10, maxit=500)
+        xh, info = s.solve_host(b_host, krylov=krylov, tol=tol, maxit=500)
         e2e.append((time.perf_counter() - t0) * 1e3)
 
     # the substitution sweeps alone (Alg. 2): HBM-bound, one graph launch each
@@ -241,31 +348,39 @@ def run_gpu(args, rank, world):
     peaks, pk_src = _peaks()
     clocks = clk.summary()
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    probes = gemm_probes()
     K = max(args.steps, 1)
-    dom = max((k for k in phmx if k not in ("upload", "assemble") and not k.startswith("host.")),
-              key=lambda k: phmx[k][0])
+    work = algorithmic_work(s, stm, nrhs)
     n_top = stmx["top_size"]
     top_flops = float(n_top) ** 3  # Cholesky n^3/3 + explicit inverse factor 2n^3/3
-    work = {"schur": stmx["schur_flops"], "qr_cluster": stmx["qr_flops"],
-            "prep": stmx["prep_flops"] - stmx["qr_flops"] - (2.0 / 3.0) * n_top ** 3,
-            "gemm_coarse": stmx["gemm_flops"], "gemm_fill": stmx["gemm_flops"],
-            "dense_top": top_flops}
+    # the dominant kernel: the device phase with the most time per step
+    dom = max((k for k in phmx if k not in ("upload", "assemble") and not k.startswith("host.")),
+              key=lambda k: phmx[k][0])
+    flops = {"prep": work["prep_flops"], "qr_cluster": work["qr_flops"],
+             "schur": work["schur_flops"], "gemm_coarse": work["gemm_flops"],
+             "gemm_fill": work["gemm_flops"], "dense_top": top_flops}
     ms_dom, nl_dom = phmx[dom][0] / K, phmx[dom][1] / K
-    fl = work.get(dom, stmx["factor_flops"])
+    fl = flops.get(dom, stmx["factor_flops"])
     ach = fl / (ms_dom * 1e-3) / 1e12
-    peak = alu_peak_tflops("f32", sm_mhz)
-    roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+    if dom == "dense_top":
+        peak, bound, psrc = probes["tf32"], "tensor", "measured: cuBLAS TF32 SGEMM 8192^3"
+    else:
+        peak, bound, psrc = probes["fp32_simt"], "alu", "measured: cuBLAS SGEMM 8192^3, TF32 off"
+    roof = {"bound": bound, "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak, "traffic": _traffic(dom, nclu_done, nl_dom),
-            "launches_per_step": nl_dom,
-            "ms_per_step": ms_dom,
-            "work": "algorithmic float32 flops per step (library counters)",
-            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x median SM clock"}
+            "launches_per_step": nl_dom, "ms_per_step": ms_dom,
+            "work": "algorithmic float32 flops per step from the factorization's ranks and "
+                    "sizes: prep 2/3 m^3 + 6 m^2 k + 2 m^3, Schur 2 f nw^2, QR 4 m c k",
+            "peak_source": psrc + " (of measured)",
+            "alu_peak_derived": alu_peak_tflops("f32", sm_mhz)}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    ab = stm["apply_bytes"] * 1.0
+    ab = work["apply_bytes"] * 1.0
     apply_gbs = ab / (apply_ms * 1e-3) / 1e9
     apply_roof = {"bound": "hbm", "kernel": "apply (all sweeps, one graph)", "achieved": apply_gbs,
                   "peak": hbm, "unit": "GB/s", "frac": apply_gbs / hbm, "ms": apply_ms,
-                  "bytes": ab, "nrhs": nrhs, "peak_source": pk_src}
+                  "bytes": ab, "operator_bytes": work["apply_operator_bytes"],
+                  "vector_bytes_per_rhs": work["apply_vector_bytes_per_rhs"], "nrhs": nrhs,
+                  "peak_source": pk_src + " (MEASURED_PEAKS.json hbm_gbs)"}
 
     def per_step(ph):
         return {k: {"ms": round(v[0] / K, 3), "launches": round(v[1] / K, 1)} for k, v in ph.items()}
@@ -286,9 +401,8 @@ def run_gpu(args, rank, world):
         "dtype": "f32+f64",
         "dtype_note": "float32 factorization and sweeps, float64 SpMV, Krylov and rank decisions",
         "data": "synthetic",
-        "config": {"workload": "3D 7-point Poisson 64^3 (N=262144), clusters of 128, eps=1e-2, "
-                               "1 RHS U[-1,1], PCG to 1e-10",
-                   "n": prob.n, "nnz": prob.nnz, "leaf": leaf, "eps": eps, "nrhs": nrhs,
+        "config": {"workload": DESCRIBE.get(args.workload, args.workload),
+                   "name": args.workload, "n": prob.n, "nnz": prob.nnz, "leaf": leaf, "eps": eps, "nrhs": nrhs,
                    "krylov": krylov, "top_size": args.top_size, "precision": args.mixed,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -296,7 +410,7 @@ def run_gpu(args, rank, world):
         "rel_residual": max(i.rel_residual for i in imx),
         "factor_ms": imx[-1].factor_ms,
         "solve_ms": imx[-1].solve_ms,
-        "fp64": {"precision": "fp64", "ms_per_step": statistics.mean(t64),
+        "fp64": {"precision": "fp64", "ms_per_step": statistics.mean(t64), "steps": fp64_steps,
                  "p50_ms": _pct(t64, 50), "p99_ms": _pct(t64, 99),
                  "iterations": i64[-1].iterations,
                  "rel_residual": max(i.rel_residual for i in i64),
@@ -318,6 +432,7 @@ def run_gpu(args, rank, world):
                   "fp64_factor_gflop": st64["factor_flops"] / 1e9},
         "clocks": clocks,
         "peaks_source": pk_src,
+        "gemm_probes": probes,
     }
     s.close()
     return res
@@ -406,33 +521,53 @@ def aggregate_replicas(res: dict, device: str = "cpu") -> dict:
     return res
 
 
-def cpu_baseline(args, steps=1):
-    """The float64 oracle on the host cores, on a bounded sample: the same
-    problem family, leaf, eps and tolerance on a 32^3 grid (N/8), with the
-    time scaled by 8 (the method's O(N) work, Sec. 4) to the 64^3 unit."""
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def oracle_sample(args, steps=1, threads=1):
+    """The float64 oracle (as it stands) on the host cores, on the bounded
+    sample of the workload: the same family, leaf, eps, Krylov method,
+    tolerance and number of right-hand sides on the grid SAMPLE_SHAPE names.
+    threads = BLAS threads the oracle's dense calls may use.  Returns the
+    measured per-step seconds (factor + solve of every right-hand side)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
     code = r"""
 import sys, time, json
 sys.path.insert(0, %r)
 import numpy as np
 from paper_1712_07297_gb300 import inputs as I
 from oracle import hsolver as H, krylov as K
-p = I.poisson((32, 32, 32))
-b = I.rhs(p.n, 1, seed=1001)[0]
+name, shape, steps, eps_arg, top = %r, %r, %d, %r, %d
+full, st = I.workload(name)
+p = I.sample_of(name, shape)
+eps = st["eps"] if eps_arg is None else eps_arg
+tol = st.get("tol", 1e-10)
+B = I.rhs(p.n, st["nrhs"], seed=st["rhs_seed"])
 A = p.scipy()
-ts = []
-for _ in range(%d):
+ts, its, res = [], 0, 0.0
+for _ in range(steps):
     t0 = time.perf_counter()
-    fac = H.factor(p.rowptr, p.col, p.val, p.coords, 128, %r, symmetric=True, top_size=%d)
-    x, it, res = K.pcg(A, b, lambda r: H.solve(fac, r), tol=1e-10, maxit=500)
+    fac = H.factor(p.rowptr, p.col, p.val, p.coords, st["leaf"], eps, symmetric=p.spd,
+                   top_size=top if p.spd else 0)
+    for b in B:
+        if st["krylov"] == "pcg":
+            x, it, r = K.pcg(A, b, lambda v: H.solve(fac, v), tol=tol, maxit=500)
+        else:
+            x, it, r = K.fgmres(A, b, lambda v: H.solve(fac, v), tol=tol, maxit=500, restart=50)
+        its, res = max(its, it), max(res, r)
     ts.append(time.perf_counter() - t0)
-print(json.dumps({"s": ts, "it": it, "res": res}))
-""" % (ROOT, steps, args.eps if args.eps is not None else 1e-2, args.top_size)
+print(json.dumps({"s": ts, "it": its, "res": res, "n": p.n, "n_full": full.n}))
+""" % (ROOT, args.workload, tuple(SAMPLE_SHAPE[args.workload]), steps, args.eps,
+       args.top_size)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         return None, r.stderr[-400:]
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d, None
+    return json.loads(r.stdout.strip().splitlines()[-1]), None
+
+
+def _sample_text(args, d):
+    shp = "x".join(map(str, SAMPLE_SHAPE[args.workload]))
+    return (f"same family, leaf, eps, Krylov method, tolerance and right-hand sides on a "
+            f"{shp} grid (N={d['n']}); measured ms per factor+solve of the sample x "
+            f"{d['n_full'] / d['n']:.0f} (N ratio: the method's O(N) cost, Sec. 4)")
 
 
 def main():
@@ -445,6 +580,8 @@ def main():
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--nrhs", type=int, default=0)
     ap.add_argument("--mixed", default="mixed_fp32")
+    ap.add_argument("--fp64-steps", dest="fp64_steps", type=int, default=2,
+                    help="timed steps of the float64 comparison path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", dest="serving_requests", type=int, default=2000)
     ap.add_argument("--serving-rate", dest="serving_rate", type=float, default=200.0)
@@ -460,21 +597,27 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        d, err = cpu_baseline(args, steps=max(1, args.steps))
+        # one BLAS thread: the oracle's many small dense calls run slower with
+        # more (32^3 sample: 8.9 s on one thread, 34 s on eight)
+        ncores = 1
+        d, err = oracle_sample(args, steps=max(1, args.steps), threads=ncores)
         if d is None:
             print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + err}))
             return
-        ms = [8 * t * 1e3 for t in d["s"]]
+        scale = d["n_full"] / d["n"]
+        ms = [scale * t * 1e3 for t in d["s"]]
         v = statistics.mean(ms)
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": v, "unit": "ms",
             "n_gpus": world, "steps": len(ms), "warmup": 0, "ms_per_step": v,
             "p50_ms": _pct(ms, 50), "p99_ms": _pct(ms, 99), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "3D 7-point Poisson 64^3 (N=262144), clusters of 128, "
-                                   "eps=1e-2, 1 RHS U[-1,1], PCG to 1e-10"},
-            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
-                             "sample": "3D Poisson 32^3 (N/8), same leaf/eps/tol, time x 8"},
+            "config": {"workload": DESCRIBE.get(args.workload, args.workload),
+                       "name": args.workload},
+            "extrapolated": True,
+            "sample_ms": [t * 1e3 for t in d["s"]],
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": ncores, "kind": "oracle",
+                             "sample": _sample_text(args, d)},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "iterations": d["it"], "rel_residual": d["res"]}))
         return
@@ -501,14 +644,16 @@ def main():
         aggregate_replicas(res, device="cuda")
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            d, err = cpu_baseline(args, steps=1)
-            if d is not None:
-                v = 8 * d["s"][0] * 1e3
-                res["cpu_baseline"] = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
-                                       "sample": "3D Poisson 32^3 (N/8), same leaf/eps/tol, "
-                                                 "time x 8 (O(N) work, Sec. 4)"}
-            else:
-                res["cpu_baseline"] = {"value": None, "error": err}
+            base = {}
+            for label, th in (("one_core", 1),):
+                d, err = oracle_sample(args, steps=1, threads=th)
+                if d is None:
+                    base[label] = {"value": None, "error": err}
+                    continue
+                v = d["n_full"] / d["n"] * d["s"][0] * 1e3
+                base[label] = {"value": v, "unit": "ms", "cores": th, "kind": "oracle",
+                               "sample_ms": d["s"][0] * 1e3, "sample": _sample_text(args, d)}
+            res["cpu_baseline"] = dict(base.get("one_core", {}))
         print(json.dumps(res))
     if world > 1:
         import torch.distributed as dist

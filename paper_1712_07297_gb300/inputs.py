@@ -221,8 +221,33 @@ def workload(name: str):
         "vcdiff3d_96": (lambda: vc_diffusion((96, 96, 96), seed=2002), dict(leaf=128, eps=1e-2, nrhs=1, krylov="pcg", rhs_seed=1002, equilibrate=1)),
         "convdiff3d_64": (lambda: convection_diffusion((64, 64, 64), 10.0), dict(leaf=128, eps=1e-2, nrhs=1, krylov="gmres", rhs_seed=1002)),
         "poisson3d_128": (lambda: poisson((128, 128, 128)), dict(leaf=128, eps=1e-2, nrhs=8, krylov="gmres", rhs_seed=1003)),
+        # the paper's indefinite Helmholtz problem (Sec. 5.1): -Lap - k^2 at
+        # 32 grid points per wavelength, GMRES to 1e-3
+        "helmholtz3d_64": (lambda: helmholtz((64, 64, 64), helmholtz_k2(32.0)), dict(leaf=128, eps=1e-2, nrhs=1, krylov="gmres", rhs_seed=1004, tol=1e-3)),
+        "helmholtz3d_32": (lambda: helmholtz((32, 32, 32), helmholtz_k2(32.0)), dict(leaf=128, eps=1e-2, nrhs=1, krylov="gmres", rhs_seed=1004, tol=1e-3)),
     }[name]
     return w[0](), dict(w[1])
+
+
+def helmholtz_k2(points_per_wavelength: float) -> float:
+    """k^2 h^2 of the unscaled Helmholtz stencil for a wavelength of the given
+    number of grid spacings: k h = 2 pi / points_per_wavelength."""
+    return (2.0 * np.pi / points_per_wavelength) ** 2
+
+
+def sample_of(name: str, shape) -> Problem:
+    """The problem family of workload `name` on a smaller grid (the bounded
+    sample the CPU oracle is timed on)."""
+    shape = tuple(int(x) for x in shape)
+    if name.startswith("poisson"):
+        return poisson(shape)
+    if name.startswith("vcdiff"):
+        return vc_diffusion(shape, seed=2002)
+    if name.startswith("convdiff"):
+        return convection_diffusion(shape, 10.0)
+    if name.startswith("helmholtz"):
+        return helmholtz(shape, helmholtz_k2(32.0))
+    raise KeyError(name)
 
 
 # The serving stream: six matrix families (2D Poisson 32^2, 128^2, 512^2; 3D
