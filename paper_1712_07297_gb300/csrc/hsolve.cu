@@ -8,6 +8,8 @@
 // hsolve_apply    Alg. 2 forward/backward substitution.
 // hsolve_solve    Sec. 5 usage: preconditioned CG / flexible GMRES in float64.
 #include <algorithm>
+#include <condition_variable>
+#include <functional>
 #include <type_traits>
 #include <atomic>
 #include <chrono>
@@ -218,6 +220,7 @@ struct hsolve_handle {
   DevBuf ws, wsd, blob_dev, blob2, blob3, cnt;
   DevBuf top_w;  // scratch of the tensor-core dense top
   PinnedBuf pin, pin2, pin3;
+  PinnedBuf pin_rank;  // ranks and error words copied back class by class
   // CUDA graphs of the substitution sweeps, one per nrhs (dropped whenever
   // the factorization or the level buffers change)
   bool use_graphs = true;
@@ -409,24 +412,84 @@ void resolve_pending(hsolve_handle* h) {
   h->pending.clear();
 }
 
-// Run f(i) for i in [0, n) on up to 16 host threads (chunks of 16 indices);
-// f must not throw.
+// A process-wide pool of host worker threads for the factorization's
+// parallel loops (started on first use, never stopped: the threads wait on a
+// condition variable and touch no CUDA state).  One loop runs on it at a
+// time; a loop that finds it busy (another handle factoring in another
+// thread) runs on its caller alone.
+class WorkerPool {
+ public:
+  explicit WorkerPool(int nt) {
+    for (int t = 0; t < nt; t++)
+      th_.emplace_back([this] {
+        uint64_t seen = 0;
+        while (true) {
+          std::function<void(int)>* job;
+          int n;
+          {
+            std::unique_lock<std::mutex> lk(mu_);
+            cv_.wait(lk, [&] { return gen_ != seen; });
+            seen = gen_;
+            job = job_;
+            n = n_;
+          }
+          drain(job, n);
+          {
+            std::lock_guard<std::mutex> lk(mu_);
+            if (--active_ == 0) done_.notify_all();
+          }
+        }
+      });
+  }
+  int size() const { return (int)th_.size(); }
+  // Run f(i) for i in [0, n) on the pool and the caller; false if busy.
+  bool run(int n, std::function<void(int)>& f) {
+    std::unique_lock<std::mutex> busy(busy_, std::try_to_lock);
+    if (!busy.owns_lock()) return false;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      job_ = &f;
+      n_ = n;
+      next_.store(0);
+      active_ = (int)th_.size();
+      gen_++;
+    }
+    cv_.notify_all();
+    drain(&f, n);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [&] { return active_ == 0; });
+    return true;
+  }
+
+ private:
+  void drain(std::function<void(int)>* f, int n) {
+    for (int i0; (i0 = next_.fetch_add(16)) < n;)
+      for (int i = i0; i < std::min(n, i0 + 16); i++) (*f)(i);
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_, busy_;
+  std::condition_variable cv_, done_;
+  std::function<void(int)>* job_ = nullptr;
+  int n_ = 0, active_ = 0;
+  uint64_t gen_ = 0;
+  std::atomic<int> next_{0};
+};
+
+WorkerPool& worker_pool() {
+  static WorkerPool* pool = new WorkerPool(
+      (int)std::min(15u, std::max(1u, std::thread::hardware_concurrency()) - 1));
+  return *pool;
+}
+
+// Run f(i) for i in [0, n) on the worker pool (chunks of 16 indices); small
+// loops, or a busy pool, run on the caller.  f must not throw.
 template <typename F>
 void parallel_for(int n, F&& f) {
-  int nt = (int)std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
-  nt = std::min(nt, std::max(1, n / 32));
-  if (nt <= 1) {
-    for (int i = 0; i < n; i++) f(i);
-    return;
+  if (n >= 48 && worker_pool().size() > 0) {
+    std::function<void(int)> fn = [&f](int i) { f(i); };
+    if (worker_pool().run(n, fn)) return;
   }
-  std::atomic<int> next(0);
-  std::vector<std::thread> th;
-  for (int t = 0; t < nt; t++)
-    th.emplace_back([&] {
-      for (int i0; (i0 = next.fetch_add(16)) < n;)
-        for (int i = i0; i < std::min(n, i0 + 16); i++) f(i);
-    });
-  for (auto& x : th) x.join();
+  for (int i = 0; i < n; i++) f(i);
 }
 
 // Host wall time of a section, added to the phase table as "host.<name>"
@@ -455,6 +518,16 @@ void check_dev_error(hsolve_handle* h) {
                                           " at level " + std::to_string(e.level) +
                                           ", cluster " + std::to_string(e.cluster));
   }
+}
+
+// A copy of the device error word taken behind a class's kernels.
+void check_err_copy(const DevError& e) {
+  if (e.code != 0)
+    throw Fail((hsolve_status)e.code, std::string(e.code == HSOLVE_ERR_NOT_SPD
+                                                      ? "Cholesky pivot not positive"
+                                                      : "zero pivot in LU") +
+                                          " at level " + std::to_string(e.level) +
+                                          ", cluster " + std::to_string(e.cluster));
 }
 
 // ---------------------------------------------------------------------------
@@ -551,42 +624,45 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   int64_t vmap_n = 0;
   std::vector<int> fillcols(nc, 0), fillw(nc, 0), nzcols(nc, -1);
   FL.cls.clear();
-  // rank-independent part of every cluster's tasks, built in parallel: its
-  // pattern row without the diagonal (neighbour or fill block, both block
-  // offsets) and, for every ordered pair of its neighbours, the offset of
-  // their block (the Schur-complement targets)
+  // rank-independent part of every cluster's tasks, built in parallel for
+  // the whole level: its pattern row without the diagonal (neighbour or fill
+  // block, both block offsets) and, for every ordered pair of its
+  // neighbours, the offset of their block (the Schur-complement targets)
   struct NbPre {
     int j, kind;
     int64_t p_sj, p_js;
   };
   std::vector<std::vector<NbPre>> pre_nb(nc);
   std::vector<std::vector<int64_t>> pre_sb(nc);
+  auto prepass = [&](int s) {
+    auto& L = pre_nb[s];
+    L.clear();
+    int nn = 0;
+    for (int p = P.ptr[s]; p < P.ptr[s + 1]; p++) {
+      const int j = P.col[p];
+      if (j == s) continue;
+      L.push_back({j, (int)P.kind[p], P.off[p], P.off[P.find(j, s)]});
+      nn += P.kind[p] == 1;
+    }
+    auto& sb = pre_sb[s];
+    sb.resize((size_t)nn * nn);
+    int a = 0;
+    for (auto& ea : L) {
+      if (ea.kind != 1) continue;
+      int b = 0;
+      for (auto& eb : L) {
+        if (eb.kind != 1) continue;
+        const int64_t q = P.find(ea.j, eb.j);
+        sb[(size_t)a * nn + b] = q < 0 ? -1 : P.off[q];
+        b++;
+      }
+      a++;
+    }
+  };
   {
     HostTimer ht(h, "host.prepass");
     parallel_for(nc, [&](int s) {
-      if (P.m[s] == 0) return;
-      auto& L = pre_nb[s];
-      int nn = 0;
-      for (int p = P.ptr[s]; p < P.ptr[s + 1]; p++) {
-        const int j = P.col[p];
-        if (j == s) continue;
-        L.push_back({j, (int)P.kind[p], P.off[p], P.off[P.find(j, s)]});
-        nn += P.kind[p] == 1;
-      }
-      auto& sb = pre_sb[s];
-      sb.resize((size_t)nn * nn);
-      int a = 0;
-      for (auto& ea : L) {
-        if (ea.kind != 1) continue;
-        int b = 0;
-        for (auto& eb : L) {
-          if (eb.kind != 1) continue;
-          const int64_t q = P.find(ea.j, eb.j);
-          sb[(size_t)a * nn + b] = q < 0 ? -1 : P.off[q];
-          b++;
-        }
-        a++;
-      }
+      if (P.m[s] > 0) prepass(s);
     });
   }
   // a single large SPD cluster (the dense top of Alg. 1) goes to the blocked
@@ -622,34 +698,112 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     h->apply_bytes += (int64_t)sizeof(real) * 2 * ((int64_t)n * n + 2 * (int64_t)n);
   }
   struct Nb { int j, w; int64_t p_sj, p_js; int ia; };
-  std::vector<Nb> nbN, nbW;
-  for (size_t c = 0; c < P.classes.size() && !dense_top; c++) {
-    std::unique_ptr<HostTimer> hb(new HostTimer(h, "host.build"));
+  // Every cluster's tasks are built in parallel with offsets relative to the
+  // cluster (its gathered-column runs, workspace, norms workspace, Schur
+  // block bases and neighbour lds, vector-map entries), then concatenated in
+  // cluster order with the offsets rebased.
+  struct ClusterBuild {
+    PrepTask pt;
+    SketchTask sk;
+    GemmTask gY, gXT, gE, gE2;
+    SchurTask sc;
+    bool has_sk = false, has_Y = false, has_E = false, has_sc = false;
+    std::vector<Seg> segs;
+    std::vector<int64_t> sbase;
+    std::vector<int> sld;
+    std::vector<ScatterSeg> segN, segW;
+    std::vector<std::pair<int, int>> nbs;  // neighbours (id, width), column order
+    int64_t ws = 0, wsd = 0;
+    int nw = 0, nwf = 0, maxw = 0;
+    bool bad = false;
+  };
+  std::vector<ClusterBuild> cbs_keep;
+  // The classes run as a pipeline between host and device: a class's ranks
+  // are final once its pivoted QR has run (the cluster-QR kernel, or the
+  // per-cluster kernel where the QR runs inside it), so they are copied back
+  // right then, and the host builds the next class's tasks while the device
+  // still runs this class's remaining kernels.  Device errors (a failed
+  // Cholesky or LU pivot) are copied back behind each class and read one
+  // class later.
+  struct ClassTasks {
     std::vector<int> S;
-    for (int s : P.classes[c])
-      if (cur[s] > 0) S.push_back(s);
-    if (S.empty()) continue;
-    FL.cls.push_back(S);
-    const int nt = (int)S.size();
-    std::vector<PrepTask> prep(nt);
+    int nt = 0;
+    std::vector<PrepTask> prep;
     std::vector<SketchTask> sk;
     int maxl = 0;
     std::vector<GemmTask> gY, gXT, gE, gE2;
     std::vector<SchurTask> sch;
     std::vector<ScatterSeg> segN, segW;
-    std::vector<Seg> segs;  // runs of gathered columns, task by task
+    std::vector<Seg> segs;
     std::vector<int64_t> sbase;
     std::vector<int> sld;
     int64_t ws_e = 0, wsd_e = 0;
     int maxm = 0, maxnw = 0, maxnwf = 0, maxw_seg = 0;
-    for (int t = 0; t < nt; t++) {
+    Blob b;
+    size_t o_sk = 0, o_prep = 0, o_gY = 0, o_gXT = 0, o_gE = 0, o_gE2 = 0, o_sch = 0,
+           o_segN = 0, o_segW = 0, o_segs = 0, o_sbase = 0, o_sld = 0;
+  };
+  // Tasks of the first class at or after c with clusters left; false when
+  // no class is left.
+  auto build_class = [&](size_t& c, ClassTasks& T) -> bool {
+    HostTimer hb(h, "host.build");
+    for (; c < P.classes.size(); c++) {
+      T.S.clear();
+      for (int s : P.classes[c])
+        if (cur[s] > 0) T.S.push_back(s);
+      if (!T.S.empty()) break;
+    }
+    if (c >= P.classes.size()) return false;
+    const std::vector<int>& S = T.S;
+    FL.cls.push_back(S);
+    const int nt = (int)S.size();
+    T.nt = nt;
+    std::vector<PrepTask>& prep = T.prep;
+    prep.assign(nt, PrepTask{});
+    std::vector<SketchTask>& sk = T.sk;
+    int& maxl = T.maxl;
+    std::vector<GemmTask>&gY = T.gY, &gXT = T.gXT, &gE = T.gE, &gE2 = T.gE2;
+    std::vector<SchurTask>& sch = T.sch;
+    std::vector<ScatterSeg>&segN = T.segN, &segW = T.segW;
+    std::vector<Seg>& segs = T.segs;
+    std::vector<int64_t>& sbase = T.sbase;
+    std::vector<int>& sld = T.sld;
+    int64_t &ws_e = T.ws_e, &wsd_e = T.wsd_e;
+    int &maxm = T.maxm, &maxnw = T.maxnw, &maxnwf = T.maxnwf, &maxw_seg = T.maxw_seg;
+    sk.clear();
+    gY.clear();
+    gXT.clear();
+    gE.clear();
+    gE2.clear();
+    sch.clear();
+    segN.clear();
+    segW.clear();
+    segs.clear();
+    sbase.clear();
+    sld.clear();
+    maxl = 0;
+    ws_e = wsd_e = 0;
+    maxm = maxnw = maxnwf = maxw_seg = 0;
+    // Every cluster's tasks are built in parallel with offsets relative to
+    // the cluster (its gathered-column runs, workspace, norms workspace,
+    // Schur block bases and neighbour lds, vector-map entries), then
+    // concatenated in cluster order with the offsets rebased.
+    if ((int)cbs_keep.size() < nt) cbs_keep.resize(nt);
+    std::vector<ClusterBuild>& cbs = cbs_keep;  // kept across classes (capacities reused)
+    std::unique_ptr<HostTimer> hpar(new HostTimer(h, "host.b_par"));
+    parallel_for(nt, [&](int t) {
+      ClusterBuild& cb = cbs[t];
+      cb.has_sk = cb.has_Y = cb.has_E = cb.has_sc = cb.bad = false;
+      cb.segs.clear();
+      cb.sbase.clear();
+      cb.sld.clear();
+      cb.segN.clear();
+      cb.segW.clear();
+      cb.nbs.clear();
+      cb.maxw = 0;
       const int s = S[t];
       const int m = cur[s];
-      maxm = std::max(maxm, m);
-      std::vector<Nb>& N = nbN;  // reused across clusters (capacity kept)
-      std::vector<Nb>& W = nbW;
-      N.clear();
-      W.clear();
+      std::vector<Nb> N, W;
       int nn_all = 0;  // neighbours in the pattern (index base of pre_sb)
       for (auto& e0 : pre_nb[s]) {
         const int ia = e0.kind == 1 ? nn_all++ : -1;
@@ -661,14 +815,13 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       int nw = 0, nwf = 0;
       for (auto& e : N) nw += e.w;
       for (auto& e : W) nwf += e.w;
-      fillw[s] = nwf;
-      fillcols[s] = sym ? nwf : 2 * nwf;
-      maxnw = std::max(maxnw, nw);
-      maxnwf = std::max(maxnwf, nwf);
+      cb.nw = nw;
+      cb.nwf = nwf;
       // gathered-column runs, one per block: G = [A_sw columns, (general)
       // rows of A_ws]; its first nfs runs alone are A_sW (for C U^T A_sW);
       // A_ws^T alone (for the general far-to-coarse product); A_sN columns;
       // (general) rows of A_Ns
+      std::vector<Seg>& segs = cb.segs;
       auto add_runs = [&](const std::vector<Nb>& L, bool trans, int c0) {
         for (auto& e : L) {
           Seg g{};
@@ -691,9 +844,11 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       add_runs(N, false, 0);
       const int64_t ncol1 = (int64_t)segs.size();
       if (!sym) add_runs(N, true, 0);
-      // workspace
+      // workspace (offsets relative to the cluster's share)
       const int64_t mm = (int64_t)m * m;
-      PrepTask& pt = prep[t];
+      int64_t ws_e = 0;
+      PrepTask& pt = cb.pt;
+      pt = PrepTask{};
       pt.s = s;
       pt.m = m;
       pt.ld = P.ld[s];
@@ -708,9 +863,9 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       ws_e += mm;
       pt.D2 = ws_e;
       ws_e += mm;
-      int64_t Eoff = ws_e;
+      const int64_t Eoff = ws_e;
       ws_e += (int64_t)m * std::max(nwf, 1);
-      int64_t E2off = ws_e;
+      const int64_t E2off = ws_e;
       if (!sym) ws_e += (int64_t)m * std::max(nwf, 1);
       ws_e = (ws_e + 3) / 4 * 4;
       // randomized compression: sketch Y = G Omega when G is wider than m + 8
@@ -721,19 +876,20 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         pt.Y = ws_e;
         ws_e += (int64_t)m * pt.l;
         ws_e = (ws_e + 3) / 4 * 4;
-        SketchTask t{};
-        t.m = m;
-        t.l = pt.l;
-        t.ncol = ncolG;
-        t.gcol = gcol;
-        t.nseg = ngcol;
-        t.Y = pt.Y;
-        sk.push_back(t);
-        maxl = std::max(maxl, pt.l);
+        SketchTask& k = cb.sk;
+        k = SketchTask{};
+        k.m = m;
+        k.l = pt.l;
+        k.ncol = ncolG;
+        k.gcol = gcol;
+        k.nseg = ngcol;
+        k.Y = pt.Y;
+        cb.has_sk = true;
       }
+      cb.ws = ws_e;
       pt.qr = 0;
-      pt.wsd = wsd_e;
-      wsd_e += 2 * (int64_t)std::max(ncolG, m + kSketchOversample) + 4 * m + 8;
+      pt.wsd = 0;
+      cb.wsd = 2 * (int64_t)std::max(ncolG, m + kSketchOversample) + 4 * m + 8;
       pt.T = oT[s];
       pt.TR = sym ? oT[s] : oTR[s];
       // Y = T' A_sN  (rows 0..k coarse rows, rows k.. = B_R)
@@ -741,24 +897,22 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         GemmTask g{};
         g.s = s; g.M = m; g.N = nw; g.K = m; g.mode = 0; g.lda = m; g.ldc = m;
         g.A = oT[s]; g.C = oY[s]; g.bcol = ncol0; g.nseg = (int)N.size();
-        gY.push_back(g);
-        if (!sym) {
-          g.A = oTR[s]; g.C = oXT[s]; g.bcol = ncol1;
-          gXT.push_back(g);
-        }
+        cb.gY = g;
+        g.A = sym ? 0 : oTR[s]; g.C = sym ? 0 : oXT[s]; g.bcol = ncol1;
+        cb.gXT = g;
+        cb.has_Y = true;
       }
       // E = D A_sW (coarse-to-far rows), E2 = D2 A_wsT (far-to-coarse cols)
       if (nwf > 0) {
         GemmTask g{};
         g.s = s; g.M = m; g.N = nwf; g.K = m; g.mode = 1; g.lda = m; g.ldc = m;
         g.A = pt.D; g.C = Eoff; g.bcol = gcol; g.nseg = (int)W.size();
-        gE.push_back(g);
-        if (!sym) {
-          g.A = pt.D2; g.C = E2off; g.bcol = gcolT;
-          gE2.push_back(g);
-        }
+        cb.gE = g;
+        g.A = pt.D2; g.C = E2off; g.bcol = gcolT;
+        cb.gE2 = g;
+        cb.has_E = true;
       }
-      // scatter segments
+      // scatter segments (the fill ones read the workspace: rebased later)
       int c0 = 0;
       for (auto& e : N) {
         ScatterSeg sg{};
@@ -767,8 +921,8 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         sg.src2 = sym ? -1 : oXT[s] + (int64_t)c0 * m;
         sg.ld_src = m; sg.m = m;
         sg.dst_row = e.p_sj; sg.dst_col = e.p_js;
-        segN.push_back(sg);
-        maxw_seg = std::max(maxw_seg, e.w);
+        cb.segN.push_back(sg);
+        cb.maxw = std::max(cb.maxw, e.w);
         c0 += e.w;
       }
       c0 = 0;
@@ -779,8 +933,8 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         sg.src2 = sym ? -1 : E2off + (int64_t)c0 * m;
         sg.ld_src = m; sg.m = m;
         sg.dst_row = e.p_sj; sg.dst_col = e.p_js;
-        segW.push_back(sg);
-        maxw_seg = std::max(maxw_seg, e.w);
+        cb.segW.push_back(sg);
+        cb.maxw = std::max(cb.maxw, e.w);
         c0 += e.w;
       }
       // Schur task: maps and block bases
@@ -790,41 +944,163 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         sc.P = sym ? oY[s] : oXT[s];
         sc.Q = oY[s];
         sc.map = ncol0;  // the A_sN runs: one per neighbour, colstart = its offset
-        sc.base = (int64_t)sbase.size();
+        sc.base = 0;
         const auto& sb = pre_sb[s];
         for (int a = 0; a < (int)N.size(); a++)
           for (int b = 0; b < (int)N.size(); b++) {
             const int64_t o = sb[(size_t)N[a].ia * nn_all + N[b].ia];
-            if (o < 0) throw Fail(HSOLVE_ERR_CUDA, "internal: missing Schur target block");
-            sbase.push_back(o);
+            if (o < 0) cb.bad = true;
+            cb.sbase.push_back(o);
           }
+        sc.ldn = 0;
+        for (auto& e : N) cb.sld.push_back(P.ld[e.j]);
+        cb.sc = sc;
+        cb.has_sc = true;
+      }
+      for (auto& e : N) cb.nbs.push_back({e.j, e.w});
+    });
+    hpar.reset();
+    std::unique_ptr<HostTimer> hmerge(new HostTimer(h, "host.b_merge"));
+    for (int t = 0; t < nt; t++) {
+      ClusterBuild& cb = cbs[t];
+      if (cb.bad) throw Fail(HSOLVE_ERR_CUDA, "internal: missing Schur target block");
+      const int s = S[t];
+      const int m = cur[s];
+      maxm = std::max(maxm, m);
+      maxnw = std::max(maxnw, cb.nw);
+      maxnwf = std::max(maxnwf, cb.nwf);
+      maxw_seg = std::max(maxw_seg, cb.maxw);
+      fillw[s] = cb.nwf;
+      fillcols[s] = sym ? cb.nwf : 2 * cb.nwf;
+      const int64_t sg0 = (int64_t)segs.size(), W0 = ws_e;
+      PrepTask pt = cb.pt;
+      pt.gcol += sg0;
+      pt.ws += W0;
+      pt.D += W0;
+      pt.D2 += W0;
+      if (pt.l > 0) pt.Y += W0;
+      pt.wsd = wsd_e;
+      prep[t] = pt;
+      if (cb.has_sk) {
+        SketchTask k = cb.sk;
+        k.gcol += sg0;
+        k.Y += W0;
+        sk.push_back(k);
+        maxl = std::max(maxl, k.l);
+      }
+      if (cb.has_Y) {
+        GemmTask g = cb.gY;
+        g.bcol += sg0;
+        gY.push_back(g);
+        if (!sym) {
+          g = cb.gXT;
+          g.bcol += sg0;
+          gXT.push_back(g);
+        }
+      }
+      if (cb.has_E) {
+        GemmTask g = cb.gE;
+        g.A += W0;
+        g.C += W0;
+        g.bcol += sg0;
+        gE.push_back(g);
+        if (!sym) {
+          g = cb.gE2;
+          g.A += W0;
+          g.C += W0;
+          g.bcol += sg0;
+          gE2.push_back(g);
+        }
+      }
+      segN.insert(segN.end(), cb.segN.begin(), cb.segN.end());
+      for (ScatterSeg sg : cb.segW) {
+        sg.src += W0;
+        if (sg.src2 >= 0) sg.src2 += W0;
+        segW.push_back(sg);
+      }
+      if (cb.has_sc) {
+        SchurTask sc = cb.sc;
+        sc.map += sg0;
+        sc.base = (int64_t)sbase.size();
         sc.ldn = (int64_t)sld.size();
-        for (auto& e : N) sld.push_back(P.ld[e.j]);
+        sbase.insert(sbase.end(), cb.sbase.begin(), cb.sbase.end());
+        sld.insert(sld.end(), cb.sld.begin(), cb.sld.end());
         sch.push_back(sc);
       }
+      segs.insert(segs.end(), cb.segs.begin(), cb.segs.end());
+      ws_e += cb.ws;
+      wsd_e += cb.wsd;
       // apply record (k filled after the class completes)
       ApplyRec& r = recs[s];
-      r.m = m; r.k = 0; r.nw = nw; r.sym = sym ? 1 : 0;
+      r.m = m; r.k = 0; r.nw = cb.nw; r.sym = sym ? 1 : 0;
       r.voff = P.voff[s];
       r.T = oT[s]; r.TR = sym ? oT[s] : oTR[s];
       r.Y = oY[s]; r.XT = sym ? oY[s] : oXT[s];
       r.map = vmap_n;
-      for (auto& e : N) {
-        vruns.push_back({vmap_n, P.voff[e.j], e.w, 0});
-        vmap_n += e.w;
-        nbl[s].push_back({e.j, e.w});
+      for (auto& e : cb.nbs) {
+        vruns.push_back({vmap_n, P.voff[e.first], e.second, 0});
+        vmap_n += e.second;
+        nbl[s].push_back(e);
       }
     }
-    // ---- upload this class's task arrays
-    Blob b;
-    size_t o_sk = b.add(sk);
-    size_t o_prep = b.add(prep), o_gY = b.add(gY), o_gXT = b.add(gXT), o_gE = b.add(gE),
-           o_gE2 = b.add(gE2), o_sch = b.add(sch), o_segN = b.add(segN), o_segW = b.add(segW),
-           o_segs = b.add(segs), o_sbase = b.add(sbase), o_sld = b.add(sld);
-    h->ws.ensure(std::max<int64_t>(ws_e, 4) * sizeof(real));
-    h->wsd.ensure(std::max<int64_t>(wsd_e, 4) * sizeof(double));
-    char* d = upload_blob(h, b);
-    hb.reset();
+    hmerge.reset();
+    Blob& b = T.b;
+    b.h.clear();
+    T.o_sk = b.add(sk);
+    T.o_prep = b.add(prep);
+    T.o_gY = b.add(gY);
+    T.o_gXT = b.add(gXT);
+    T.o_gE = b.add(gE);
+    T.o_gE2 = b.add(gE2);
+    T.o_sch = b.add(sch);
+    T.o_segN = b.add(segN);
+    T.o_segW = b.add(segW);
+    T.o_segs = b.add(segs);
+    T.o_sbase = b.add(sbase);
+    T.o_sld = b.add(sld);
+    return true;
+  };
+  h->pin_rank.ensure(sizeof(int) * std::max(nc, 1) + 2 * sizeof(DevError));
+  int* krank = reinterpret_cast<int*>(h->pin_rank.p);
+  DevError* kerr = reinterpret_cast<DevError*>(krank + std::max(nc, 1));  // 2 slots
+  cudaEvent_t ev_rank = nullptr;
+  HS_CUDA(cudaEventCreateWithFlags(&ev_rank, cudaEventDisableTiming));
+  struct EventGuard {
+    cudaEvent_t e;
+    ~EventGuard() { cudaEventDestroy(e); }
+  } ev_guard{ev_rank};
+  ClassTasks TA, TB;
+  ClassTasks* Tc = &TA;
+  ClassTasks* Tn = &TB;
+  size_t cidx = 0;
+  int nclass = 0;
+  bool have = !dense_top && build_class(cidx, *Tc);
+  while (have) {
+    ClassTasks& T = *Tc;
+    const std::vector<int>& S = T.S;
+    const int nt = T.nt;
+    std::vector<PrepTask>& prep = T.prep;
+    const std::vector<SketchTask>& sk = T.sk;
+    const int maxl = T.maxl;
+    const std::vector<GemmTask>&gY = T.gY, &gXT = T.gXT, &gE = T.gE, &gE2 = T.gE2;
+    const std::vector<SchurTask>& sch = T.sch;
+    const std::vector<ScatterSeg>&segN = T.segN, &segW = T.segW;
+    const int maxm = T.maxm, maxnw = T.maxnw, maxnwf = T.maxnwf, maxw_seg = T.maxw_seg;
+    const size_t o_sk = T.o_sk, o_prep = T.o_prep, o_gY = T.o_gY, o_gXT = T.o_gXT,
+                 o_gE = T.o_gE, o_gE2 = T.o_gE2, o_sch = T.o_sch, o_segN = T.o_segN,
+                 o_segW = T.o_segW, o_segs = T.o_segs, o_sbase = T.o_sbase, o_sld = T.o_sld;
+    h->ws.ensure(std::max<int64_t>(T.ws_e, 4) * sizeof(real));
+    h->wsd.ensure(std::max<int64_t>(T.wsd_e, 4) * sizeof(double));
+    char* d = upload_blob(h, T.b);
+    // the ranks are final after the pivoted QR: in the cluster-QR kernel,
+    // unless some cluster's QR runs inside the per-cluster kernel
+    bool rank_in_prep = !sk.empty() || !h->opts.cluster_qr;
+    bool rank_copied = false;
+    auto copy_ranks = [&] {
+      HS_CUDA(cudaMemcpyAsync(krank, rank, sizeof(int) * nc, cudaMemcpyDeviceToHost, h->st));
+      HS_CUDA(cudaEventRecord(ev_rank, h->st));
+      rank_copied = true;
+    };
     real* ws = h->ws.as<real>();
     const PrepTask* d_prep = reinterpret_cast<const PrepTask*>(d + o_prep);
     const Seg* d_segs = reinterpret_cast<const Seg*>(d + o_segs);
@@ -890,6 +1166,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
                                    h->wsd.as<double>(), d_segs, rank, pivd, fpiv,
                                    h->cnt.as<int>(), eps, max_rank_arg, h->st);
         });
+        if (!rank_in_prep) copy_ranks();
       }
     }
     if (!sk.empty())
@@ -908,6 +1185,7 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
                          h->wsd.as<double>(), d_segs, rank, pivd, fpiv, eps, sym ? 1 : 0,
                          max_rank_arg, maxm, h->d_err.as<DevError>(), level, dbg, h->st);
     });
+    if (!rank_copied) copy_ranks();
     if (dbg) {
       // per checkpoint interval: the slowest cluster of the class, in ms at
       // the 2.07 GHz maximum SM clock
@@ -959,16 +1237,16 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
                             reinterpret_cast<const int64_t*>(d + o_sbase),
                             reinterpret_cast<const int*>(d + o_sld), rank, h->st);
     });
-    // ---- ranks of this class (the next class's neighbour widths need them)
-    std::vector<int> kk(nc);
-    {
-      HostTimer ht(h, "host.rank_copy");
-      HS_CUDA(cudaMemcpyAsync(kk.data(), rank, sizeof(int) * nc, cudaMemcpyDeviceToHost, h->st));
-    }
+    if (!rank_copied) copy_ranks();
+    // the error word behind this class's kernels (read one class later)
+    HS_CUDA(cudaMemcpyAsync(kerr + (nclass & 1), h->d_err.p, sizeof(DevError),
+                            cudaMemcpyDeviceToHost, h->st));
     {
       HostTimer ht(h, "host.wait_rank");
-      check_dev_error(h);  // synchronises the stream
+      HS_CUDA(cudaEventSynchronize(ev_rank));
     }
+    if (nclass > 0) check_err_copy(kerr[(nclass - 1) & 1]);
+    std::vector<int> kk(krank, krank + nc);
     for (int s : S) {
       FL.k[s] = kk[s];
       cur[s] = kk[s];
@@ -1000,6 +1278,15 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
         h->apply_bytes += (int64_t)sizeof(real) * 2 * (2 * (int64_t)m + 2 * (int64_t)nw);
       }
     }
+    nclass++;
+    cidx++;
+    have = build_class(cidx, *Tn);  // overlaps this class's remaining kernels
+    std::swap(Tc, Tn);
+  }
+  if (nclass > 0) {
+    HostTimer ht(h, "host.wait_last");
+    HS_CUDA(cudaStreamSynchronize(h->st));
+    check_err_copy(kerr[(nclass - 1) & 1]);
   }
   // ---- apply records and maps for this level
   HostTimer ht_end(h, "host.level_end");
@@ -1104,8 +1391,12 @@ void build_next(hsolve_handle* h, FLevel& FL, const real* arena, std::unique_ptr
     if (h->pcache.size() >= 32) h->pcache.erase(h->pcache.begin());
     h->pcache.push_back({to_top, kin, P.m, P.ptr, P.col, Q});
   }
-  out_arena.alloc(Q.arena_elems * sizeof(real));
+  {
+    HostTimer ht(h, "host.next_alloc");
+    out_arena.alloc(Q.arena_elems * sizeof(real));
+  }
   HS_CUDA(cudaMemsetAsync(out_arena.p, 0, Q.arena_elems * sizeof(real), h->st));
+  HostTimer ht_tasks(h, "host.next_tasks");
   std::vector<CopyTask> tasks;
   for (int a = 0; a < nc; a++) {
     if (kin[a] == 0) continue;
@@ -1135,11 +1426,12 @@ void build_next(hsolve_handle* h, FLevel& FL, const real* arena, std::unique_ptr
     });
   }
   // vector gather map: next-level position -> this level's position
+  HostTimer ht_idx(h, "host.next_idx");
+  // children of parent I are contiguous in a (2I, 2I+1; every a for the
+  // top), so one pass in order lists them parent by parent
   std::vector<int64_t> idx;
-  for (int I = 0; I < Q.nclu; I++)
-    for (int a = 0; a < nc; a++)
-      if (parent(a) == I)
-        for (int i = 0; i < kin[a]; i++) idx.push_back(P.voff[a] + i);
+  for (int a = 0; a < nc; a++)
+    for (int i = 0; i < kin[a]; i++) idx.push_back(P.voff[a] + i);
   FL.next_n = (int64_t)idx.size();
   FL.next_idx.alloc(sizeof(int64_t) * std::max<size_t>(idx.size(), 1));
   if (!idx.empty())
@@ -1225,7 +1517,10 @@ void factor_impl(hsolve_handle* h, double eps) {
     }
     h->F.push_back(std::move(cur));
     cur = std::move(nxt);
-    arena = std::move(narena);
+    {
+      HostTimer ht(h, "host.arena_free");
+      arena = std::move(narena);
+    }
     level++;
   }
   HS_CUDA(cudaEventRecord(e1, h->st));

@@ -63,13 +63,27 @@ fwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
   real acc[RB];
 #pragma unroll
   for (int r = 0; r < RB; r++) acc[r] = 0;
-  if (i < m)
-    for (int l = part; l < m; l += 4) {
-      const real t = T[i + (int64_t)l * m];
+  if (i < m) {
+    // four independent loads in flight per step
+    int l = part;
+    for (; l + 12 < m; l += 16) {
+      const real t0 = __ldg(T + i + (int64_t)l * m);
+      const real t1 = __ldg(T + i + (int64_t)(l + 4) * m);
+      const real t2 = __ldg(T + i + (int64_t)(l + 8) * m);
+      const real t3 = __ldg(T + i + (int64_t)(l + 12) * m);
+#pragma unroll
+      for (int r = 0; r < RB; r++)
+        if (r < g.nr)
+          acc[r] += t0 * ys[r * m + l] + t1 * ys[r * m + l + 4] + t2 * ys[r * m + l + 8] +
+                    t3 * ys[r * m + l + 12];
+    }
+    for (; l < m; l += 4) {
+      const real t = __ldg(T + i + (int64_t)l * m);
 #pragma unroll
       for (int r = 0; r < RB; r++)
         if (r < g.nr) acc[r] += t * ys[r * m + l];
     }
+  }
 #pragma unroll
   for (int r = 0; r < RB; r++) red[r][threadIdx.x] = acc[r];
   __syncthreads();
@@ -145,8 +159,18 @@ bwd_part_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
     real acc[RB];
 #pragma unroll
     for (int r = 0; r < RB; r++) acc[r] = 0;
-    for (int c = 0; c < nc; c++) {
-      const real b = BR[i + (int64_t)(c0 + c) * m];
+    const real* Bi = BR + i + (int64_t)c0 * m;
+    int c = 0;
+    // four independent loads in flight per step
+    for (; c + 3 < nc; c += 4) {
+      const real b0 = __ldg(Bi + (int64_t)c * m), b1 = __ldg(Bi + (int64_t)(c + 1) * m);
+      const real b2 = __ldg(Bi + (int64_t)(c + 2) * m), b3 = __ldg(Bi + (int64_t)(c + 3) * m);
+#pragma unroll
+      for (int r = 0; r < RB; r++)
+        acc[r] += b0 * xn[r][c] + b1 * xn[r][c + 1] + b2 * xn[r][c + 2] + b3 * xn[r][c + 3];
+    }
+    for (; c < nc; c++) {
+      const real b = __ldg(Bi + (int64_t)c * m);
 #pragma unroll
       for (int r = 0; r < RB; r++) acc[r] += b * xn[r][c];
     }
