@@ -39,6 +39,48 @@ struct RhsGroup {
       : r0(blockIdx.z * rb), nr(min(rb, nrhs - (int)blockIdx.z * rb)) {}
 };
 
+// Sums of RB values over a warp.  RB = 8: a reduce-scatter butterfly (9
+// shuffles instead of 8 x 5): each exchange halves the set of values a lane
+// carries, lane l ending with the total of value rs_index(l); lanes 0..7
+// hold the 8 totals once each.  RB = 1: the plain butterfly in every lane.
+__device__ __forceinline__ int rs_index(int lane) {
+  return ((lane & 1) << 2) | (lane & 2) | ((lane & 4) >> 2);
+}
+
+template <typename real>
+__device__ __forceinline__ real warp_sum8(const real (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+  real a[4], b[2];
+  const bool h1 = lane & 1, h2 = lane & 2, h4 = lane & 4;
+#pragma unroll
+  for (int j = 0; j < 4; j++)
+    a[j] = (h1 ? v[4 + j] : v[j]) + __shfl_xor_sync(0xffffffffu, h1 ? v[j] : v[4 + j], 1);
+#pragma unroll
+  for (int j = 0; j < 2; j++)
+    b[j] = (h2 ? a[2 + j] : a[j]) + __shfl_xor_sync(0xffffffffu, h2 ? a[j] : a[2 + j], 2);
+  real c = (h4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h4 ? b[0] : b[1], 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 8);
+  c += __shfl_xor_sync(0xffffffffu, c, 16);
+  return c;
+}
+
+// Reduce acc[0..RB) over the warp; returns the total that this lane reports
+// and sets *r to its right-hand side (-1: this lane reports nothing).
+template <typename real, int RB>
+__device__ __forceinline__ real warp_sums(real (&acc)[RB], int* r) {
+  const int lane = threadIdx.x & 31;
+  if constexpr (RB == 8) {
+    const real t = warp_sum8<real>(acc);
+    *r = lane < 8 ? rs_index(lane) : -1;
+    return t;
+  } else {
+    real t = acc[0];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    *r = lane == 0 ? 0 : -1;
+    return t;
+  }
+}
+
 template <typename real, int RB>
 __global__ void __launch_bounds__(256)
 fwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
@@ -98,6 +140,9 @@ __global__ void __launch_bounds__(256)
 fwd_nbr_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
                const real* __restrict__ fac, const int64_t* __restrict__ vmap,
                real* __restrict__ y, const real* __restrict__ z, int64_t ldy, int nrhs, int rb) {
+  extern __shared__ unsigned char smem_raw[];
+  real* zsh = reinterpret_cast<real*>(smem_raw);  // RB x f: z_f, read once per CTA
+  __shared__ real dsh[RB][kCols];                 // the column sums of this CTA
   const ApplyRec rc = recs[ids[blockIdx.y]];
   const int m = rc.m, k = rc.k, f = m - k;
   if (k == m) return;
@@ -109,10 +154,13 @@ fwd_nbr_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
   const int c0 = blockIdx.x * kCols;
   if (c0 >= rc.nw) return;
   const int c1 = min(rc.nw, c0 + kCols);
+  for (int r = 0; r < g.nr; r++)
+    for (int i = threadIdx.x; i < f; i += blockDim.x)
+      zsh[r * f + i] = z[rc.voff + k + i + (int64_t)(g.r0 + r) * ldy];
+  __syncthreads();
   const real* BL = fac + (rc.sym ? rc.Y : rc.XT) + k;  // column c: B_L[c, :]
   const int64_t* vm = vmap + rc.map;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const real* zf = z + rc.voff + k + (int64_t)g.r0 * ldy;
   for (int c = c0 + warp; c < c1; c += nwarp) {
     const real* col = BL + (int64_t)c * m;
     real acc[RB];
@@ -122,15 +170,19 @@ fwd_nbr_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
       const real b = col[i];
 #pragma unroll
       for (int r = 0; r < RB; r++)
-        if (r < g.nr) acc[r] += b * zf[i + (int64_t)r * ldy];
+        if (r < g.nr) acc[r] += b * zsh[r * f + i];
     }
-#pragma unroll
-    for (int r = 0; r < RB; r++)
-      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-    if (lane == 0)
-#pragma unroll
-      for (int r = 0; r < RB; r++)
-        if (r < g.nr) y[vm[c] + (int64_t)(g.r0 + r) * ldy] -= acc[r];
+    int rr;
+    const real t = warp_sums<real, RB>(acc, &rr);
+    if (rr >= 0) dsh[rr][c - c0] = t;
+  }
+  __syncthreads();
+  // y_N -= B_L z_f: every thread one (column, right-hand side) of the CTA;
+  // the neighbour slots of a column range are contiguous runs
+  const int nc = c1 - c0;
+  for (int e = threadIdx.x; e < nc * g.nr; e += blockDim.x) {
+    const int c = e % nc, r = e / nc;
+    y[vm[c0 + c] + (int64_t)(g.r0 + r) * ldy] -= dsh[r][c];
   }
 }
 
@@ -234,13 +286,9 @@ bwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
       for (int r = 0; r < RB; r++)
         if (r < g.nr) acc[r] += t * zsm[r * m + l];
     }
-#pragma unroll
-    for (int r = 0; r < RB; r++)
-      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-    if (lane == 0)
-#pragma unroll
-      for (int r = 0; r < RB; r++)
-        if (r < g.nr) y[rc.voff + i + (int64_t)(g.r0 + r) * ldy] = acc[r];
+    int rr;
+    const real tot = warp_sums<real, RB>(acc, &rr);
+    if (rr >= 0 && rr < g.nr) y[rc.voff + i + (int64_t)(g.r0 + rr) * ldy] = tot;
   }
 }
 
@@ -287,13 +335,9 @@ bwd_zt_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
       for (int r = 0; r < RB; r++)
         if (r < g.nr) acc[r] += t * zsm[r * m + l];
     }
-#pragma unroll
-    for (int r = 0; r < RB; r++)
-      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-    if (lane == 0)
-#pragma unroll
-      for (int r = 0; r < RB; r++)
-        if (r < g.nr) y[rc.voff + i + (int64_t)(g.r0 + r) * ldy] = acc[r];
+    int rr;
+    const real tot = warp_sums<real, RB>(acc, &rr);
+    if (rr >= 0 && rr < g.nr) y[rc.voff + i + (int64_t)(g.r0 + rr) * ldy] = tot;
   }
 }
 
@@ -332,8 +376,9 @@ void launch_fwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int ma
   count_launch();
   fwd_t_kernel<real, RB><<<g1, 256, sm, st>>>(recs, ids, fac, y, z, ldy, nrhs, rb);
   dim3 g2(std::max(1, (maxnw + kCols - 1) / kCols), nids, nz);
+  set_smem<fwd_nbr_kernel<real, RB>>();
   count_launch();
-  fwd_nbr_kernel<real, RB><<<g2, 256, 0, st>>>(recs, ids, fac, vmap, y, z, ldy, nrhs, rb);
+  fwd_nbr_kernel<real, RB><<<g2, 256, sm, st>>>(recs, ids, fac, vmap, y, z, ldy, nrhs, rb);
 }
 
 template <typename real, int RB>
