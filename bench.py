@@ -211,17 +211,27 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-def _traffic(kernel, nclu, launches):
+def _traffic(kernel, workload, nclu, launches):
     """DRAM bytes per launch of the dominant kernel from its committed ncu
-    summary (measured on a smaller case and scaled by the clusters a launch
-    processes here), or None when no summary gives a per-cluster figure."""
+    summary under profiles/: a figure captured on this workload
+    ("traffic_bytes_per_launch(<workload>): N"), else a per-cluster figure
+    measured on a smaller case and scaled by the clusters a launch processes
+    here ("traffic_bytes_per_cluster: N"); None when no summary gives one."""
     import glob
     import re
-    if kernel != "prep" or not launches:
+    names = {"schur": "schur_kernel", "prep": "prep_kernel", "qr_cluster": "qr_cluster_kernel"}
+    stem = names.get(kernel)
+    if not stem:
         return None
-    for f in glob.glob(os.path.join(ROOT, "profiles", "prep_kernel*.md")):
-        m = re.search(r"traffic_bytes_per_cluster:\s*(\d+)", open(f).read())
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        txt = open(f).read()
+        m = re.search(r"%s.*?traffic_bytes_per_launch\(%s\):\s*(\d+)" % (stem, re.escape(workload)),
+                      txt, re.S)
         if m:
+            return int(m.group(1))
+    for f in glob.glob(os.path.join(ROOT, "profiles", stem + "*.md")):
+        m = re.search(r"traffic_bytes_per_cluster:\s*(\d+)", open(f).read())
+        if m and launches:
             return int(m.group(1)) * nclu / launches
     return None
 
@@ -367,7 +377,7 @@ def run_gpu(args, rank, world):
     else:
         peak, bound, psrc = probes["fp32_simt"], "alu", "measured: cuBLAS SGEMM 8192^3, TF32 off"
     roof = {"bound": bound, "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": _traffic(dom, nclu_done, nl_dom),
+            "frac": ach / peak, "traffic": _traffic(dom, args.workload, nclu_done, nl_dom),
             "launches_per_step": nl_dom, "ms_per_step": ms_dom,
             "work": "algorithmic float32 flops per step from the factorization's ranks and "
                     "sizes: prep 2/3 m^3 + 6 m^2 k + 2 m^3, Schur 2 f nw^2, QR 4 m c k",

@@ -52,11 +52,14 @@ def _ranks_bounded(s):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed_fp32"])
 def test_poisson3d_64(hs, precision):
-    # 3D 7-point Poisson 64^3, clusters of 128, eps in {1e-2, 1e-4}, 1 and 16 RHS
+    # 3D 7-point Poisson 64^3, clusters of 128, eps in {1e-2, 1e-4, 0}, 1 and
+    # 16 RHS; eps = 0 keeps every nonzero direction: a direct solver, so the
+    # Krylov method needs one step in float64 and a few in float32 (the
+    # preconditioner is then exact up to float32 rounding)
     p, st = I.workload("poisson3d_64")
     s = hs.Solver.from_problem(p, leaf_size=128, symmetric=1, top_size=8192)
     its = []
-    for eps in (1e-2, 1e-4):
+    for eps in (1e-2, 1e-4, 0.0):
         s.factor(eps, precision)
         _ranks_bounded(s)
         for nrhs in (1, 16):
@@ -67,7 +70,8 @@ def test_poisson3d_64(hs, precision):
                 its.append(info.iterations)
         if eps == 1e-2:
             _check_spd_preconditioner(s, p.n)
-    assert its[1] <= its[0]
+    assert its[2] <= its[1] <= its[0]
+    assert its[2] <= (1 if precision == "fp64" else 3)
     s.close()
 
 
@@ -107,4 +111,23 @@ def test_poisson3d_128_mixed_8rhs(hs):
     b = I.rhs(p.n, 8, seed=1003)
     x, info = s.solve(torch.from_numpy(b).cuda(), krylov="gmres", tol=1e-10, maxit=300)
     _check_residual(p, b, x.cpu().numpy(), 1e-10)
+    s.close()
+
+
+def test_helmholtz3d_32_gmres(hs):
+    # the paper's Helmholtz problem -Lap - k^2 (Sec. 5.1) at 32 grid points
+    # per wavelength (indefinite on this grid: k^2 h^2 = 0.0386 exceeds the
+    # smallest Laplacian eigenvalue 0.0272), general (LU, two-sided) path,
+    # GMRES to 1e-3 as the paper runs it, and to 1e-10 with the same
+    # factorization
+    p, st = I.workload("helmholtz3d_32")
+    assert not p.spd
+    s = hs.Solver.from_problem(p, leaf_size=st["leaf"], symmetric=0)
+    for prec in ("fp64", "mixed_fp32"):
+        s.factor(st["eps"], prec)
+        _ranks_bounded(s)
+        b = I.rhs(p.n, 2, seed=st["rhs_seed"])
+        for tol in (st["tol"], 1e-10):
+            x, info = s.solve(torch.from_numpy(b).cuda(), krylov="gmres", tol=tol, maxit=500)
+            _check_residual(p, b, x.cpu().numpy(), tol)
     s.close()

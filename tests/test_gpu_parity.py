@@ -108,12 +108,15 @@ def test_eps0_is_direct(hs):
 @pytest.mark.parametrize("mk,leaf,eps", [
     (lambda: I.convection_diffusion((16, 16, 16), 10.0), 64, 1e-2),
     (lambda: I.convection_diffusion((40, 30), 10.0), 32, 1e-3),
+    # the paper's Helmholtz operator at 32 points per wavelength (still
+    # definite on this small grid; from 32^3 on it is indefinite), LU path
+    (lambda: I.helmholtz((16, 16, 16), I.helmholtz_k2(32.0)), 64, 1e-2),
 ])
 def test_general_matches_oracle(hs, mk, leaf, eps):
     # nonsymmetric: pivot orders of the LU factors may legitimately differ on
     # near-ties, so the comparison is on M^{-1} b, which does not depend on them
     p = mk()
-    fac = _oracle(p, leaf, eps)
+    fac = H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=False)
     s = hs.Solver.from_problem(p, leaf_size=leaf, symmetric=0)
     s.factor(eps, "fp64")
     _ranks_match(s, fac)

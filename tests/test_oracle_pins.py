@@ -17,7 +17,8 @@ from oracle import matrix_form as MF
 
 
 def _fac(p, leaf, eps, **kw):
-    return H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=p.symmetric, **kw)
+    # Cholesky path for SPD problems, LU (two-sided) otherwise
+    return H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=p.spd, **kw)
 
 
 def _minv(p, leaf, eps, **kw):
@@ -31,6 +32,9 @@ SMALL = [
     (lambda: I.convection_diffusion((6, 6, 6), 10.0), 14),
     (lambda: I.convection_diffusion((12, 12), 10.0), 9),
     (lambda: I.high_contrast((8, 8, 8), seed=2), 16),
+    # symmetric indefinite: -Lap - k^2 with k^2 h^2 = 2 (several negative
+    # eigenvalues on this grid), through the LU path
+    (lambda: I.helmholtz((6, 6, 6), 2.0), 14),
 ]
 
 
