@@ -412,6 +412,21 @@ hsolve_status hsolve_export_level(const hsolve_handle* h, int level, hsolve_leve
                                   hsolve_cluster_export* clusters, double* fac,
                                   int32_t* pivots, int32_t* nbr_id, int32_t* nbr_w);
 
+/* One cluster of hsolve_export_level without copying the whole level: its
+ * record into *rec (offsets relative to this cluster's own arrays: T and TR
+ * at 0, Y and XT at 0 when present, -1 when absent; piv and nb at 0) and,
+ * where the pointer is not NULL, its blocks converted to float64 into
+ * caller-owned HOST arrays -- T (m x m), TRt (m x m, general only), Y
+ * (m x nw), XT (m x nw, general only), all column-major with leading
+ * dimension m -- its pivots (k entries) and neighbours (nnb ids and widths).
+ * Call with NULL arrays first to learn m, nw, k and nnb.  Errors:
+ * HSOLVE_ERR_ARG (level or cluster out of range), HSOLVE_ERR_STATE,
+ * HSOLVE_ERR_CUDA. */
+hsolve_status hsolve_export_cluster(const hsolve_handle* h, int level, int cluster,
+                                    hsolve_cluster_export* rec, double* T, double* TRt,
+                                    double* Y, double* XT, int32_t* pivots, int32_t* nbr_id,
+                                    int32_t* nbr_w);
+
 /* Level-0 cluster of every unknown: perm[p] = global index of the unknown at
  * position p of the cluster-ordered vector (host array of n entries). */
 hsolve_status hsolve_get_perm(const hsolve_handle* h, int64_t* perm);

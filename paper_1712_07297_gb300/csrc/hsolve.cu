@@ -2531,6 +2531,74 @@ hsolve_status hsolve_export_level(const hsolve_handle* hc, int level, hsolve_lev
   return HSOLVE_OK;
 }
 
+hsolve_status hsolve_export_cluster(const hsolve_handle* hc, int level, int cluster,
+                                    hsolve_cluster_export* rec, double* T, double* TRt,
+                                    double* Y, double* XT, int32_t* pivots, int32_t* nbr_id,
+                                    int32_t* nbr_w) {
+  hsolve_handle* h = const_cast<hsolve_handle*>(hc);
+  if (!h || !rec) return HSOLVE_ERR_ARG;
+  if (!h->factored) return set_err(h, HSOLVE_ERR_STATE, "export before factor");
+  if (level < 0 || level >= (int)h->F.size()) return set_err(h, HSOLVE_ERR_ARG, "no such level");
+  const FLevel& F = *h->F[level];
+  if (cluster < 0 || cluster >= F.P.nclu) return set_err(h, HSOLVE_ERR_ARG, "no such cluster");
+  std::memset(rec, 0, sizeof(*rec));
+  rec->T = rec->TR = rec->Y = rec->XT = -1;
+  rec->colour = cluster < (int)F.P.colour.size() ? F.P.colour[cluster] : 0;
+  if (F.hrecs.empty()) return HSOLVE_OK;  // a level that only merged into the top
+  const ApplyRec& r = F.hrecs[cluster];
+  rec->m = r.m;
+  rec->k = r.m > 0 ? r.k : 0;
+  rec->nw = r.nw;
+  rec->nnb = F.nb_ptr[cluster + 1] - F.nb_ptr[cluster];
+  rec->npiv = rec->k;
+  const bool have = r.m > 0 && r.k < r.m;
+  if (have) {
+    rec->T = 0;
+    if (!r.sym) rec->TR = 0;
+    if (r.nw > 0) {
+      rec->Y = 0;
+      if (!r.sym) rec->XT = 0;
+    }
+  }
+  const size_t esz = h->prec == HSOLVE_FP64 ? sizeof(double) : sizeof(float);
+  try {
+    auto fetch = [&](int64_t off, int64_t elems, double* dst) {
+      if (!dst || off < 0 || elems <= 0) return;
+      std::vector<char> buf((size_t)elems * esz);
+      HS_CUDA(cudaMemcpyAsync(buf.data(), F.fac.as<char>() + off * (int64_t)esz, buf.size(),
+                              cudaMemcpyDeviceToHost, h->st));
+      HS_CUDA(cudaStreamSynchronize(h->st));
+      if (esz == sizeof(double)) {
+        std::memcpy(dst, buf.data(), buf.size());
+      } else {
+        const float* f = reinterpret_cast<const float*>(buf.data());
+        for (int64_t i = 0; i < elems; i++) dst[i] = f[i];
+      }
+    };
+    if (have) {
+      const int64_t mm = (int64_t)r.m * r.m, mw = (int64_t)r.m * r.nw;
+      fetch(r.T, mm, T);
+      if (!r.sym) fetch(r.TR, mm, TRt);
+      fetch(r.Y, mw, Y);
+      if (!r.sym) fetch(r.XT, mw, XT);
+    }
+    if (pivots && rec->k > 0) {
+      std::vector<int> pv(rec->k);
+      HS_CUDA(cudaMemcpyAsync(pv.data(), F.piv.as<int>() + F.P.voff[cluster], sizeof(int) * pv.size(),
+                              cudaMemcpyDeviceToHost, h->st));
+      HS_CUDA(cudaStreamSynchronize(h->st));
+      for (int j = 0; j < rec->k; j++) pivots[j] = pv[j];
+    }
+    for (int q = 0; q < rec->nnb; q++) {
+      if (nbr_id) nbr_id[q] = F.nb_id[F.nb_ptr[cluster] + q];
+      if (nbr_w) nbr_w[q] = F.nb_w[F.nb_ptr[cluster] + q];
+    }
+  } catch (const Fail& f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return HSOLVE_OK;
+}
+
 hsolve_status hsolve_get_perm(const hsolve_handle* h, int64_t* perm) {
   if (!h || !perm) return HSOLVE_ERR_ARG;
   std::memcpy(perm, h->perm.data(), sizeof(int64_t) * h->n);

@@ -93,6 +93,9 @@ EXPORTS = {
     "hsolve_get_perm": (C.c_int, [C.c_void_p, C.c_void_p]),
     "hsolve_export_level": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(LevelExport), C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hsolve_export_cluster": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(ClusterExport),
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "hsolve_get_phase_times": (C.c_int, [C.c_void_p, C.POINTER(PhaseTime), C.c_int32,
                                          C.POINTER(C.c_int32)]),
     "hsolve_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
@@ -364,6 +367,33 @@ class Solver:
                 XT=blk(r.XT, m, r.nw)))
         return dict(nclu=nc, dense_top=bool(info.dense_top), symmetric=bool(info.symmetric),
                     precision=info.precision, clusters=out)
+
+    def export_cluster(self, level: int, cluster: int) -> dict:
+        """One cluster's record and blocks (hsolve_export_cluster): the same
+        keys as a cluster of export_level."""
+        lib = load()
+        r = ClusterExport()
+        _check(lib.hsolve_export_cluster(self.h, level, cluster, C.byref(r), None, None, None,
+                                         None, None, None, None), self.h)
+        m, k, nw, nnb = r.m, r.k, r.nw, r.nnb
+        T = np.zeros(max(m * m, 1)) if r.T >= 0 else None
+        TRt = np.zeros(max(m * m, 1)) if r.TR >= 0 else None
+        Y = np.zeros(max(m * nw, 1)) if r.Y >= 0 else None
+        XT = np.zeros(max(m * nw, 1)) if r.XT >= 0 else None
+        piv = np.zeros(max(k, 1), dtype=np.int32)
+        nid = np.zeros(max(nnb, 1), dtype=np.int32)
+        nwd = np.zeros(max(nnb, 1), dtype=np.int32)
+        ptr = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+        _check(lib.hsolve_export_cluster(self.h, level, cluster, C.byref(r), ptr(T), ptr(TRt),
+                                         ptr(Y), ptr(XT), piv.ctypes.data, nid.ctypes.data,
+                                         nwd.ctypes.data), self.h)
+
+        def mat(a, cols):
+            return None if a is None else a[:m * cols].reshape(cols, m).T.copy()
+
+        return dict(m=m, k=k, nw=nw, colour=r.colour, piv=piv[:k].copy(),
+                    nbrs=list(zip(nid[:nnb].tolist(), nwd[:nnb].tolist())),
+                    T=mat(T, m), TRt=mat(TRt, m), Y=mat(Y, nw), XT=mat(XT, nw))
 
     def perm(self) -> np.ndarray:
         p = np.zeros(self.n, dtype=np.int64)
