@@ -397,3 +397,22 @@ def test_forced_ranks_match_oracle(hs, precision, bound, name, mk, leaf, eps):
     out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
     assert _rel(out, ref) < bound, _rel(out, ref)
     s.close()
+
+
+def test_float32_noise_floor_matches_the_float64_one(hs):
+    # a fill block that is zero in exact arithmetic but nonzero through
+    # rounding (2D upwind convection-diffusion, level 1) must not get a rank
+    # from the noise: the oracle drops it through its float64 floor (1e-14
+    # max |A_ss|), the float32 path through its own (1e-6 max |A_ss|, the
+    # float32 rounding level of such a block); both give k = 0 there
+    p = I.convection_diffusion((30, 30), 10.0)
+    fac = H.factor(p.rowptr, p.col, p.val, p.coords, 32, 1e-3, symmetric=False)
+    lv = fac.levels[1]
+    noisy = [i for i, cf in lv.factors.items() if cf.k == 0 and cf.ncols_fill > 0]
+    assert noisy
+    for prec in ("fp64", "mixed_fp32"):
+        s = hs.Solver.from_problem(p, leaf_size=32, symmetric=0)
+        s.factor(1e-3, prec)
+        _, ranks, _ = s.level(1)
+        assert all(ranks[i] == 0 for i in noisy), (prec, [int(ranks[i]) for i in noisy])
+        s.close()
