@@ -60,9 +60,10 @@ Readings of points the paper leaves open:
     display); fine-to-far coupling is dropped.
   * Next level's A_B: block (I, J) is present iff some child pair (a, b) was
     within block distance two at this level and both kept coarse DOFs.
-  * Top: when one cluster is left, or (SPD matrices) the level holds at most
-    ``top_size`` DOFs, the whole level is factored densely (Alg. 1, "small
-    enough"); a general matrix keeps the hierarchy down to one cluster.
+  * Top: when one cluster is left, or the level holds at most ``top_size``
+    DOFs, the whole level is factored densely (Alg. 1, "small enough": a size
+    test, the same for SPD and general matrices): Cholesky, or LU with
+    partial pivoting for a general matrix (Sec. 6).
   * Alg. 2's backward sweep: the coarse system is solved before W_i^T is
     applied for i = m-1..0 -- the order that inverts the factorization of
     Alg. 1 (A^fac = W_0^{-1} .. W_{m-1}^{-1} diag(I, A_c^fac) W_{m-1}^{-T} ..).
@@ -509,7 +510,7 @@ def factor(prob_rowptr, prob_col, prob_val, coords, leaf: int, eps: float,
         offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         d2 = distance2(adj)
         live = int(np.count_nonzero(sizes))
-        if nclu == 1 or live <= 1 or (symmetric and offsets[-1] <= top_size):
+        if nclu == 1 or live <= 1 or offsets[-1] <= top_size:
             top = _dense_top(blocks, sizes, symmetric)
             levels.append(Level(nclu, sizes, offsets, adj, d2, [0] * nclu, list(range(nclu)), {},
                                 np.zeros(nclu, dtype=np.int64), top))

@@ -241,12 +241,45 @@ def test_fixed_rank_caps_ranks():
     assert max(f.k for f in fac.levels[0].factors.values()) <= 3
 
 
-def test_dense_top_switch():
-    p = I.poisson((12, 12))
+@pytest.mark.parametrize("mk", [lambda: I.poisson((12, 12)),
+                                lambda: I.convection_diffusion((12, 12)),
+                                lambda: I.helmholtz((6, 6, 6), 2.0)])
+def test_dense_top_switch(mk):
+    # Alg. 1's "small enough" test is a size test for SPD and general
+    # matrices alike: a level of at most top_size unknowns is factored
+    # densely (Cholesky, or LU with partial pivoting), and that dense factor
+    # is exact
+    p = mk()
     b = I.rhs(p.n, 1, seed=1)[0]
-    x0 = H.solve(_fac(p, 9, 0.0, top_size=10 ** 9), b)   # one dense factor
-    assert len(_fac(p, 9, 0.0, top_size=10 ** 9).levels) == 1
-    np.testing.assert_allclose(p.scipy() @ x0, b, atol=1e-12)
+    fac = _fac(p, 9, 0.0, top_size=10 ** 9)   # one dense factor
+    assert len(fac.levels) == 1
+    assert fac.levels[0].top["kind"] == ("chol" if p.spd else "lu")
+    np.testing.assert_allclose(p.scipy() @ H.solve(fac, b), b, atol=1e-11)
+    # a mid-hierarchy top: the level it is taken at is the first one of at
+    # most top_size unknowns
+    full = _fac(p, 9, 0.0)
+    sizes = [int(lv.offsets[-1]) for lv in full.levels]
+    cut = sizes[1]
+    fac = _fac(p, 9, 0.0, top_size=cut)
+    assert len(fac.levels) == 2 and fac.levels[1].top["n"] == cut
+    np.testing.assert_allclose(p.scipy() @ H.solve(fac, b), b, atol=1e-10)
+
+
+def test_lu_top_operators():
+    # A = P L U: T = L^{-1} P^T and TRt = U^{-T} give A^{-1} = TRt^T T, L is
+    # unit lower, and on an indefinite matrix partial pivoting bounds every
+    # multiplier by 1 (and does interchange rows)
+    p = I.helmholtz((6, 6, 6), 2.0)
+    fac = H.factor(p.rowptr, p.col, p.val, p.coords, 9, 0.0, symmetric=False, top_size=10 ** 9)
+    top = fac.levels[0].top
+    op = H.top_operators(top)
+    A = p.dense()[np.ix_(fac.perm, fac.perm)]
+    np.testing.assert_allclose(op["TRt"].T @ op["T"] @ A, np.eye(p.n), atol=1e-10)
+    L = top["L"]
+    np.testing.assert_array_equal(np.diag(L), 1.0)
+    assert np.abs(L).max() <= 1.0 + 1e-15
+    assert not np.array_equal(top["P"], np.eye(p.n))
+    assert np.allclose(np.triu(op["T"] @ top["P"], 1), 0.0)
 
 
 @pytest.mark.parametrize("method", ["pcg", "gmres"])
