@@ -75,11 +75,16 @@ typedef struct {
                              below it); default 128 */
   int32_t symmetric;      /* -1 = detect (exact value symmetry), 0 = general
                              (LU, two-sided compression), 1 = SPD (Cholesky) */
-  int64_t top_size;       /* SPD matrices: factor a level densely once it
-                             holds at most this many unknowns (0 = only when
-                             one cluster is left); general matrices always
-                             keep the hierarchy down to one cluster; default
-                             0 */
+  int64_t top_size;       /* factor a level densely once it holds at most
+                             this many unknowns (0 = only when one cluster
+                             is left): blocked Cholesky (SPD) or blocked LU
+                             with partial pivoting (general).  hsolve_factor
+                             rejects (HSOLVE_ERR_ARG) a value above the
+                             dense-top limit: 24,576 unknowns in fp64 and
+                             49,152 in the float32 modes (one slot vector of
+                             the sweeps in shared memory), and for a general
+                             matrix also 24,816 (the first LU panel in one
+                             16-CTA thread-block cluster); default 0 */
   int32_t max_rank;       /* > 0: cap every compression rank at this value
                              (the fixed-rank option of Sec. 5.1); 0 = none */
   int32_t gmres_restart;  /* GMRES restart length; default 50 */

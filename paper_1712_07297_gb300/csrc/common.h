@@ -239,6 +239,8 @@ struct Launch {
   static void apply_fwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int maxnw,
                         const real* fac, const int64_t* vmap, real* y, real* z, int64_t ldy,
                         int nrhs, cudaStream_t st);
+  // largest cluster the sweeps take (one slot vector in shared memory)
+  static int apply_max_m();
   static void apply_bwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int maxnw,
                         const real* fac, const int64_t* vmap, real* y, real* z, real* part,
                         int64_t ldy, int nrhs, cudaStream_t st);
@@ -258,6 +260,16 @@ struct Launch {
   // its Cholesky factor L; X (n x n, ld n) receives L^{-1}.
   static void dense_top(real* A, int64_t lda, int n, real* X, DevError* err, int level,
                         cudaStream_t st);
+  // Dense top of a general factorization: blocked LU with partial pivoting
+  // of A (n x n, ld lda, overwritten by L and U), then T = L^{-1} P and
+  // TRt = U^{-T} (n x n, ld n each; A = P^T L U).  scratch: lu_top_scratch(n)
+  // bytes.  n at most lu_top_max() (the tall panel of the first columns
+  // must fit in the shared memory of one 16-CTA thread-block cluster);
+  // false above it (nothing launched) or when a panel launch fails.
+  static int lu_top_max();
+  static size_t lu_top_scratch(int n);
+  static bool lu_top(real* A, int64_t lda, int n, real* T, real* TRt, void* scratch,
+                     DevError* err, int level, cudaStream_t st);
 };
 
 // float64 Krylov helpers (kernels.cu)

@@ -665,12 +665,28 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
       if (P.m[s] > 0) prepass(s);
     });
   }
-  // a single large SPD cluster (the dense top of Alg. 1) goes to the blocked
-  // multi-CTA Cholesky and inverse factor: E_s = I, k = 0, no neighbours
-  const bool dense_top = (nc == 1 && sym && cur[0] > kTopOneCta);
+  // a single large cluster (the dense top of Alg. 1) goes to the blocked
+  // multi-CTA Cholesky (SPD) or LU with partial pivoting (general) and the
+  // inverse factors: E_s = I, k = 0, no neighbours
+  const bool dense_top = (nc == 1 && cur[0] > kTopOneCta &&
+                          (sym || cur[0] <= Launch<real>::lu_top_max()));
   if (dense_top) {
     const int n = cur[0];
-    if (std::is_same<real, float>::value) {
+    if (!sym) {
+      h->top_w.ensure(Launch<real>::lu_top_scratch(n));
+      bool ok = true;
+      timed_lv(h, "dense_top", level, 0, [&] {
+        ok = Launch<real>::lu_top(arena + P.off[P.find(0, 0)], P.ld[0], n, fac + oT[0],
+                                  fac + oTR[0], h->top_w.p, h->d_err.as<DevError>(), level,
+                                  h->st);
+      });
+      if (!ok) {
+        const cudaError_t e = cudaGetLastError();
+        throw Fail(e == cudaSuccess ? HSOLVE_ERR_ARG : HSOLVE_ERR_CUDA,
+                   std::string("LU top: ") + (e == cudaSuccess ? "above its size limit"
+                                                              : cudaGetErrorString(e)));
+      }
+    } else if (std::is_same<real, float>::value) {
       // float32 modes: recursive Cholesky + inverse factor with tcgen05
       // 3xTF32 products (float32-level accuracy)
       h->top_w.ensure(sizeof(float) * dense_top_tc_scratch(n));
@@ -690,11 +706,13 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
     FL.k[0] = 0;
     cur[0] = 0;
     ApplyRec& r = recs[0];
-    r.m = n; r.k = 0; r.nw = 0; r.sym = 1; r.voff = 0;
-    r.T = oT[0]; r.TR = oT[0]; r.Y = oY[0]; r.XT = oY[0]; r.map = 0;
-    const double nf = n;
-    h->prep_flops += 2.0 / 3.0 * nf * nf * nf;
-    h->factor_flops += 2.0 / 3.0 * nf * nf * nf;
+    r.m = n; r.k = 0; r.nw = 0; r.sym = sym ? 1 : 0; r.voff = 0;
+    r.T = oT[0]; r.TR = sym ? oT[0] : oTR[0];
+    r.Y = oY[0]; r.XT = sym ? oY[0] : oXT[0]; r.map = 0;
+    // Cholesky n^3/3 + inverse n^3/3; LU 2n^3/3 + two inverses n^3/3 each
+    const double nf = n, fl = (sym ? 2.0 / 3.0 : 4.0 / 3.0) * nf * nf * nf;
+    h->prep_flops += fl;
+    h->factor_flops += fl;
     h->apply_bytes += (int64_t)sizeof(real) * 2 * ((int64_t)n * n + 2 * (int64_t)n);
   }
   struct Nb { int j, w; int64_t p_sj, p_js; int ia; };
@@ -1442,6 +1460,14 @@ void build_next(hsolve_handle* h, FLevel& FL, const real* arena, std::unique_ptr
 
 template <typename real>
 void factor_impl(hsolve_handle* h, double eps) {
+  // a merged dense top must fit the substitution sweeps' shared-memory slot
+  // vectors and, for a general matrix, the LU panel's thread-block cluster
+  int64_t top_max = Launch<real>::apply_max_m();
+  if (!h->symmetric) top_max = std::min<int64_t>(top_max, Launch<real>::lu_top_max());
+  if (h->opts.top_size > top_max)
+    throw Fail(HSOLVE_ERR_ARG, "top_size " + std::to_string(h->opts.top_size) +
+                                   " above the dense-top limit of " + std::to_string(top_max) +
+                                   " unknowns for this precision and matrix type");
   {
     HostTimer ht(h, "host.clear");
     h->F.clear();
@@ -1476,9 +1502,9 @@ void factor_impl(hsolve_handle* h, double eps) {
     int live = 0;
     for (int i = 0; i < P.nclu; i++) live += P.m[i] > 0;
     const int64_t vlen = P.voff[P.nclu];
-    // top_size merges an SPD level into the dense top (blocked Cholesky);
-    // a general matrix keeps the hierarchy down to one cluster
-    const bool small = (P.nclu == 1 || live <= 1 || (h->symmetric && vlen <= h->opts.top_size));
+    // a level of at most top_size unknowns merges into the dense top
+    // (blocked Cholesky or LU; top_size was checked against their limits)
+    const bool small = (P.nclu == 1 || live <= 1 || vlen <= h->opts.top_size);
     if (small && !(P.nclu == 1)) {
       // merge everything into one cluster for the dense top factor
       std::unique_ptr<FLevel> nxt;

@@ -413,6 +413,11 @@ void launch_bwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int ma
 }  // namespace
 
 template <typename real>
+int Launch<real>::apply_max_m() {
+  return (int)(kSmemCeiling / sizeof(real));
+}
+
+template <typename real>
 void Launch<real>::apply_fwd(const ApplyRec* recs, const int* ids, int nids, int maxm, int maxnw,
                              const real* fac, const int64_t* vmap, real* y, real* z, int64_t ldy,
                              int nrhs, cudaStream_t st) {

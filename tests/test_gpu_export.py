@@ -17,7 +17,9 @@ Bars:
       and last kept diagonal of the pivoted QR, at most 1/eps) for the
       basis U of the first k pivot columns, and sqrt(c) more for the
       randomized variant, whose sketch G Omega sums c gathered columns per
-      entry (rounding relative to |G||Omega|, not |G Omega|);
+      entry (rounding relative to |G||Omega|, not |G Omega|); for a general
+      matrix times max(kappa(L_F), kappa(U_F)), the LU factors of the fine
+      block F whose inverses T' and T'_R carry;
       level l > 0: the level's input already differs by the rounding of the
       levels before it, so the bound is multiplied by the product over those
       levels of their largest kappa(A_ss) max(1, r_11 / r_kk).
@@ -31,8 +33,8 @@ The cases reach the kernel branches the full-size workloads take: 3D clusters
 of 128 unknowns (the headline leaf), clusters of 216-256 unknowns (per-cluster
 matrices no longer resident in shared memory; pivoted QR on thread-block
 clusters of several CTAs), dense tops above 256 unknowns (multi-CTA dense
-factor; the two-kernel backward sweep), the general (LU, two-sided) path and
-the randomized compression.
+factor, Cholesky and LU; the two-kernel backward sweep), the general (LU,
+two-sided) path and the randomized compression.
 """
 import functools
 
@@ -52,12 +54,24 @@ C_BOUND = 2.0
 MEANINGFUL = 0.1
 
 CASES = {
-    # name: (problem, leaf, eps, top_size, compress)
-    "poisson3d_32_leaf128": (lambda: I.poisson((32, 32, 32)), 128, 1e-2, 2048, 0),
-    "poisson3d_24_leaf256": (lambda: I.poisson((24, 24, 24)), 256, 1e-2, 1500, 0),
-    "convdiff3d_16": (lambda: I.convection_diffusion((16, 16, 16), 10.0), 64, 1e-2, 0, 0),
-    "poisson3d_16_sketch": (lambda: I.poisson((16, 16, 16)), 64, 1e-2, 0, 1),
+    # name: (problem, leaf, eps, top_size, compress, symmetric (None: the
+    # matrix's own))
+    "poisson3d_32_leaf128": (lambda: I.poisson((32, 32, 32)), 128, 1e-2, 2048, 0, None),
+    "poisson3d_24_leaf256": (lambda: I.poisson((24, 24, 24)), 256, 1e-2, 1500, 0, None),
+    "convdiff3d_16": (lambda: I.convection_diffusion((16, 16, 16), 10.0), 64, 1e-2, 0, 0, None),
+    "poisson3d_16_sketch": (lambda: I.poisson((16, 16, 16)), 64, 1e-2, 0, 1, None),
+    # general matrices with a merged dense top above 256 unknowns (the
+    # blocked LU on thread-block clusters); the indefinite Helmholtz matrix
+    # (k^2 h^2 = 1) on the general path makes the top's LU interchange rows
+    "convdiff3d_20_lutop": (lambda: I.convection_diffusion((20, 20, 20), 10.0), 64, 1e-2, 2000, 0,
+                            None),
+    "helmholtz3d_16_lutop": (lambda: I.helmholtz((16, 16, 16), 1.0), 64, 1e-2, 1500, 0, False),
 }
+
+
+def _sym(name):
+    p, _ = _case(name)
+    return p.symmetric if CASES[name][5] is None else CASES[name][5]
 
 
 @pytest.fixture(scope="module")
@@ -73,17 +87,18 @@ def hs():
 
 @functools.lru_cache(maxsize=None)
 def _case(name):
-    mk, leaf, eps, top, compress = CASES[name]
+    mk, leaf, eps, top, compress, sym = CASES[name]
     p = mk()
-    fac = H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=p.symmetric,
+    sym = p.symmetric if sym is None else sym
+    fac = H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=sym,
                    top_size=top, compress=compress)
     return p, fac
 
 
 def _solver(hs, name):
     p, _ = _case(name)
-    _, leaf, _, top, compress = CASES[name]
-    return hs.Solver.from_problem(p, leaf_size=leaf, symmetric=1 if p.symmetric else 0,
+    _, leaf, _, top, compress, _ = CASES[name]
+    return hs.Solver.from_problem(p, leaf_size=leaf, symmetric=1 if _sym(name) else 0,
                                   top_size=top, compress=compress)
 
 
@@ -94,10 +109,15 @@ def _blk_err(got, ref):
     return np.abs(got - ref).max() / scale
 
 
-def _amp(cf, sketch):
-    """kappa(A_ss) max(1, r_11 / r_kk) (sqrt(c) more for a sketch)."""
+def _amp(cf, sketch, sym):
+    """kappa(A_ss) max(1, r_11 / r_kk) (sqrt(c) more for a sketch); for a
+    general matrix also max(kappa(L_F), kappa(U_F)): T' holds L_F^{-1} and
+    T'_R holds U_F^{-1}, and a triangular inverse carries the perturbation of
+    its factor multiplied by the factor's condition number."""
     a = cf.rdiag[0] / cf.rdiag[-1] if len(cf.rdiag) else 1.0
     g = np.linalg.cond(cf.Ass) * max(1.0, a)
+    if not sym and cf.LF.size:
+        g *= max(np.linalg.cond(cf.LF), np.linalg.cond(cf.UF))
     if sketch and cf.ncols_fill > cf.m + H.SKETCH_OVERSAMPLE:
         g *= np.sqrt(cf.ncols_fill)
     return g
@@ -152,7 +172,7 @@ def _compare(s, fac, sym, u, sketch=False):
             if op is None:
                 assert c["T"] is None
                 continue
-            amp = _amp(cf, sketch)
+            amp = _amp(cf, sketch, sym)
             lvl_amp = max(lvl_amp, amp)
             bound = C_BOUND * u * amp * grow
             if bound > MEANINGFUL:
@@ -175,8 +195,11 @@ def test_fp64_blocks_match_oracle(hs, name):
     s = _solver(hs, name)
     s.factor(CASES[name][2], "fp64")
     assert np.array_equal(s.perm(), fac.perm)
-    worst, nblk = _compare(s, fac, p.symmetric, U_FP64, sketch=CASES[name][4] == 1)
+    worst, nblk = _compare(s, fac, _sym(name), U_FP64, sketch=CASES[name][4] == 1)
     assert nblk > 10
+    if name.endswith("_lutop"):
+        top = fac.levels[-1].top
+        assert top["kind"] == "lu" and top["n"] > 256 and s.stats()["top_size"] == top["n"]
     print(f"{name}: fp64 {nblk} blocks, worst error {worst:.2f} of its bound")
     s.close()
 
@@ -195,7 +218,7 @@ def test_fp32_blocks_at_oracle_ranks(hs, name):
     pivs = [[list(lv.factors[i].piv) if i in lv.factors else [] for i in range(lv.nclu)]
             for lv in lvs]
     s.factor_forced("mixed_fp32", ranks, pivs)
-    worst, nblk = _compare(s, fac, p.symmetric, U_FP32)
+    worst, nblk = _compare(s, fac, _sym(name), U_FP32)
     assert nblk > 10
     print(f"{name}: fp32 forced {nblk} blocks, worst error {worst:.2f} of its bound")
     s.close()

@@ -105,21 +105,27 @@ def test_eps0_is_direct(hs):
     s.close()
 
 
-@pytest.mark.parametrize("mk,leaf,eps", [
-    (lambda: I.convection_diffusion((16, 16, 16), 10.0), 64, 1e-2),
-    (lambda: I.convection_diffusion((40, 30), 10.0), 32, 1e-3),
+@pytest.mark.parametrize("mk,leaf,eps,top", [
+    (lambda: I.convection_diffusion((16, 16, 16), 10.0), 64, 1e-2, 0),
+    (lambda: I.convection_diffusion((40, 30), 10.0), 32, 1e-3, 0),
     # the paper's Helmholtz operator at 32 points per wavelength (still
     # definite on this small grid; from 32^3 on it is indefinite), LU path
-    (lambda: I.helmholtz((16, 16, 16), I.helmholtz_k2(32.0)), 64, 1e-2),
+    (lambda: I.helmholtz((16, 16, 16), I.helmholtz_k2(32.0)), 64, 1e-2, 0),
+    # merged dense LU tops above 256 unknowns (575 and 973; the indefinite
+    # Helmholtz top interchanges rows)
+    (lambda: I.convection_diffusion((20, 20, 20), 10.0), 64, 1e-2, 2000),
+    (lambda: I.helmholtz((16, 16, 16), 1.0), 64, 1e-2, 1500),
 ])
-def test_general_matches_oracle(hs, mk, leaf, eps):
+def test_general_matches_oracle(hs, mk, leaf, eps, top):
     # nonsymmetric: pivot orders of the LU factors may legitimately differ on
     # near-ties, so the comparison is on M^{-1} b, which does not depend on them
     p = mk()
-    fac = H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=False)
-    s = hs.Solver.from_problem(p, leaf_size=leaf, symmetric=0)
+    fac = H.factor(p.rowptr, p.col, p.val, p.coords, leaf, eps, symmetric=False, top_size=top)
+    s = hs.Solver.from_problem(p, leaf_size=leaf, symmetric=0, top_size=top)
     s.factor(eps, "fp64")
     _ranks_match(s, fac)
+    if top:
+        assert s.stats()["top_size"] == fac.levels[-1].top["n"] > 256
     b = I.rhs(p.n, 2, seed=1002)
     ref = H.solve(fac, b.T).T
     out = s.apply(torch.from_numpy(b).cuda()).cpu().numpy()
@@ -129,6 +135,49 @@ def test_general_matches_oracle(hs, mk, leaf, eps):
     xx = x.cpu().numpy()
     for c in range(2):
         assert np.linalg.norm(b[c] - A @ xx[c]) <= 1.0001e-10 * np.linalg.norm(b[c])
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_fp32"])
+def test_lu_top_one_cluster(hs, precision):
+    # one cluster of 4096 unknowns: the whole matrix is the dense top (Alg. 1),
+    # factored by the blocked LU with partial pivoting whose panels span
+    # 16-CTA thread-block clusters.  An indefinite Helmholtz matrix (2D,
+    # k^2 h^2 = 0.5) makes partial pivoting interchange rows.
+    #  * A^{-1} = TRt^T T does not depend on the pivot order: within
+    #    C u kappa(A) (normwise backward stability of LU with partial
+    #    pivoting, growth included in C = 8) of the exact inverse;
+    #  * float64: T = L^{-1} P^T and TRt = U^{-T} element by element within
+    #    the same bound (the pivot orders agree: no near-ties at float64
+    #    rounding);
+    #  * the preconditioner is then a direct solver: FGMRES in one step.
+    p = I.helmholtz((64, 64), 0.5)
+    fac = H.factor(p.rowptr, p.col, p.val, p.coords, p.n, 1e-2, symmetric=False)
+    top = fac.levels[0].top
+    assert len(fac.levels) == 1 and top["kind"] == "lu" and top["n"] == p.n
+    assert not np.array_equal(top["P"], np.eye(p.n))
+    s = hs.Solver.from_problem(p, leaf_size=p.n, symmetric=0)
+    s.factor(1e-2, precision)
+    assert s.stats()["top_size"] == p.n
+    c = s.export_level(0)["clusters"][0]
+    A = p.dense()[np.ix_(fac.perm, fac.perm)]
+    Ainv = np.linalg.inv(A)
+    u = 2.0 ** -53 if precision == "fp64" else 2.0 ** -24
+    bound = 8 * u * np.linalg.cond(A)
+    err = np.abs(c["TRt"].T @ c["T"] - Ainv).max() / np.abs(Ainv).max()
+    assert err <= bound, (err, bound)
+    if precision == "fp64":
+        op = H.top_operators(top)
+        for key in ("T", "TRt"):
+            e = np.abs(c[key] - op[key]).max() / np.abs(op[key]).max()
+            assert e <= bound, (key, e, bound)
+    b = I.rhs(p.n, 2, seed=7)
+    x, info = s.solve(torch.from_numpy(b).cuda(), krylov="gmres", tol=1e-10)
+    Asp = p.scipy()
+    xx = x.cpu().numpy()
+    for k in range(2):
+        assert np.linalg.norm(b[k] - Asp @ xx[k]) <= 1.0001e-10 * np.linalg.norm(b[k])
+    assert info.iterations <= (1 if precision == "fp64" else 4)
     s.close()
 
 
