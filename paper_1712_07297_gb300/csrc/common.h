@@ -257,8 +257,10 @@ struct Launch {
   static void perm_out(const int64_t* perm, const double* S, int64_t n, const real* src,
                        int64_t lds, double* dst, int64_t ldd, int nrhs, cudaStream_t st);
   // Dense top of an SPD factorization: A (n x n, ld lda) is overwritten by
-  // its Cholesky factor L; X (n x n, ld n) receives L^{-1}.
-  static void dense_top(real* A, int64_t lda, int n, real* X, DevError* err, int level,
+  // its Cholesky factor L; X (n x n, ld n) receives L^{-1}.  W: scratch of
+  // dense_top_scratch(n) bytes.
+  static size_t dense_top_scratch(int n);
+  static void dense_top(real* A, int64_t lda, int n, real* X, real* W, DevError* err, int level,
                         cudaStream_t st);
   // Dense top of a general factorization: blocked LU with partial pivoting
   // of A (n x n, ld lda, overwritten by L and U), then T = L^{-1} P and

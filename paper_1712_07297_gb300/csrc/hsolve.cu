@@ -696,9 +696,10 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
                      h->d_err.as<DevError>(), level, h->st);
       });
     } else {
+      h->top_w.ensure(Launch<real>::dense_top_scratch(n));
       timed_lv(h, "dense_top", level, 0, [&] {
         Launch<real>::dense_top(arena + P.off[P.find(0, 0)], P.ld[0], n, fac + oT[0],
-                                h->d_err.as<DevError>(), level, h->st);
+                                h->top_w.as<real>(), h->d_err.as<DevError>(), level, h->st);
       });
     }
     check_dev_error(h);
