@@ -634,30 +634,34 @@ void factor_level(hsolve_handle* h, FLevel& FL, real* arena, int level, double e
   };
   std::vector<std::vector<NbPre>> pre_nb(nc);
   std::vector<std::vector<int64_t>> pre_sb(nc);
+  // The pair table walks each neighbour's pattern row once against a
+  // per-thread map cluster -> neighbour index (reset after every cluster)
+  // instead of searching the row for every pair.
   auto prepass = [&](int s) {
+    thread_local std::vector<int> pos;
+    if ((int)pos.size() < nc) pos.assign(nc, -1);
     auto& L = pre_nb[s];
     L.clear();
+    L.reserve(P.ptr[s + 1] - P.ptr[s]);
     int nn = 0;
     for (int p = P.ptr[s]; p < P.ptr[s + 1]; p++) {
       const int j = P.col[p];
       if (j == s) continue;
       L.push_back({j, (int)P.kind[p], P.off[p], P.off[P.find(j, s)]});
-      nn += P.kind[p] == 1;
+      if (P.kind[p] == 1) pos[j] = nn++;
     }
     auto& sb = pre_sb[s];
-    sb.resize((size_t)nn * nn);
-    int a = 0;
+    sb.assign((size_t)nn * nn, -1);
     for (auto& ea : L) {
       if (ea.kind != 1) continue;
-      int b = 0;
-      for (auto& eb : L) {
-        if (eb.kind != 1) continue;
-        const int64_t q = P.find(ea.j, eb.j);
-        sb[(size_t)a * nn + b] = q < 0 ? -1 : P.off[q];
-        b++;
+      int64_t* row = sb.data() + (size_t)pos[ea.j] * nn;
+      for (int q = P.ptr[ea.j]; q < P.ptr[ea.j + 1]; q++) {
+        const int b = pos[P.col[q]];
+        if (b >= 0) row[b] = P.off[q];
       }
-      a++;
     }
+    for (auto& ea : L)
+      if (ea.kind == 1) pos[ea.j] = -1;
   };
   {
     HostTimer ht(h, "host.prepass");
@@ -1416,25 +1420,39 @@ void build_next(hsolve_handle* h, FLevel& FL, const real* arena, std::unique_ptr
   }
   HS_CUDA(cudaMemsetAsync(out_arena.p, 0, Q.arena_elems * sizeof(real), h->st));
   HostTimer ht_tasks(h, "host.next_tasks");
-  std::vector<CopyTask> tasks;
+  // one copy per kept block, counted and then written per cluster row in
+  // parallel
+  std::vector<int64_t> tstart(nc + 1, 0);
   for (int a = 0; a < nc; a++) {
-    if (kin[a] == 0) continue;
+    int cnt = 0;
+    if (kin[a] > 0)
+      for (int p = P.ptr[a]; p < P.ptr[a + 1]; p++) cnt += kin[P.col[p]] > 0;
+    tstart[a + 1] = tstart[a] + cnt;
+  }
+  std::vector<CopyTask> tasks((size_t)tstart[nc]);
+  std::atomic<int> missing{0};
+  parallel_for(nc, [&](int a) {
+    if (kin[a] == 0) return;
+    int64_t o = tstart[a];
     for (int p = P.ptr[a]; p < P.ptr[a + 1]; p++) {
-      int b = P.col[p];
+      const int b = P.col[p];
       if (kin[b] == 0) continue;
-      int I = parent(a), J = parent(b);
-      int64_t q = Q.find(I, J);
-      if (q < 0) throw Fail(HSOLVE_ERR_CUDA, "internal: missing next-level block");
-      CopyTask t;
+      const int I = parent(a), J = parent(b);
+      const int64_t q = Q.find(I, J);
+      if (q < 0) {
+        missing.store(1);
+        return;
+      }
+      CopyTask& t = tasks[(size_t)o++];
       t.rows = kin[a];
       t.cols = kin[b];
       t.ld_src = P.ld[a];
       t.ld_dst = Q.ld[I];
       t.src = P.off[p];
       t.dst = Q.off[q] + ro[a] + (int64_t)ro[b] * Q.ld[I];
-      tasks.push_back(t);
     }
-  }
+  });
+  if (missing.load()) throw Fail(HSOLVE_ERR_CUDA, "internal: missing next-level block");
   if (!tasks.empty()) {
     Blob bl;
     size_t o = bl.add(tasks);
@@ -1448,9 +1466,14 @@ void build_next(hsolve_handle* h, FLevel& FL, const real* arena, std::unique_ptr
   HostTimer ht_idx(h, "host.next_idx");
   // children of parent I are contiguous in a (2I, 2I+1; every a for the
   // top), so one pass in order lists them parent by parent
-  std::vector<int64_t> idx;
-  for (int a = 0; a < nc; a++)
-    for (int i = 0; i < kin[a]; i++) idx.push_back(P.voff[a] + i);
+  int64_t nidx = 0;
+  for (int a = 0; a < nc; a++) nidx += kin[a];
+  std::vector<int64_t> idx((size_t)nidx);
+  {
+    int64_t o = 0;
+    for (int a = 0; a < nc; a++)
+      for (int i = 0; i < kin[a]; i++) idx[(size_t)o++] = P.voff[a] + i;
+  }
   FL.next_n = (int64_t)idx.size();
   FL.next_idx.alloc(sizeof(int64_t) * std::max<size_t>(idx.size(), 1));
   if (!idx.empty())
