@@ -214,9 +214,10 @@ class ClockSampler:
 def _traffic(kernel, workload, nclu, launches):
     """DRAM bytes per launch of the dominant kernel from its committed ncu
     summary under profiles/: a figure captured on this workload
-    ("traffic_bytes_per_launch(<workload>): N"), else a per-cluster figure
-    measured on a smaller case and scaled by the clusters a launch processes
-    here ("traffic_bytes_per_cluster: N"); None when no summary gives one."""
+    ("traffic_bytes_per_launch(<kernel>, <workload>): N"), else a per-cluster
+    figure measured on a smaller case and scaled by the clusters a launch
+    processes here ("traffic_bytes_per_cluster: N" in the kernel's own
+    summary); None when no summary gives one."""
     import glob
     import re
     names = {"schur": "schur_kernel", "prep": "prep_kernel", "qr_cluster": "qr_cluster_kernel"}
@@ -225,8 +226,8 @@ def _traffic(kernel, workload, nclu, launches):
         return None
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         txt = open(f).read()
-        m = re.search(r"%s.*?traffic_bytes_per_launch\(%s\):\s*(\d+)" % (stem, re.escape(workload)),
-                      txt, re.S)
+        m = re.search(r"traffic_bytes_per_launch\(%s, %s\):\s*(\d+)" % (stem, re.escape(workload)),
+                      txt)
         if m:
             return int(m.group(1))
     for f in glob.glob(os.path.join(ROOT, "profiles", stem + "*.md")):
@@ -392,8 +393,9 @@ def run_gpu(args, rank, world):
                   "vector_bytes_per_rhs": work["apply_vector_bytes_per_rhs"], "nrhs": nrhs,
                   "peak_source": pk_src + " (MEASURED_PEAKS.json hbm_gbs)"}
 
-    def per_step(ph):
-        return {k: {"ms": round(v[0] / K, 3), "launches": round(v[1] / K, 1)} for k, v in ph.items()}
+    def per_step(ph, nsteps):
+        return {k: {"ms": round(v[0] / nsteps, 3), "launches": round(v[1] / nsteps, 1)}
+                for k, v in ph.items()}
 
     res = {
         "metric": METRIC,
@@ -433,8 +435,8 @@ def run_gpu(args, rank, world):
         "gpu_launches_note": "library kernels per step (factor + solve), counted by the library",
         "roofline": roof,
         "apply_roofline": apply_roof,
-        "phases_mixed": per_step(phmx),
-        "phases_fp64": per_step(ph64),
+        "phases_mixed": per_step(phmx, len(tmx)),
+        "phases_fp64": per_step(ph64, len(t64)),
         "stats": {"levels": stmx["levels"], "colours_total": stmx["colours_total"],
                   "top_size": n_top, "factor_bytes": stmx["factor_bytes"],
                   "apply_bytes": stmx["apply_bytes"],

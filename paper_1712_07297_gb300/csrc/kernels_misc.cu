@@ -186,7 +186,12 @@ sketch_kernel(const SketchTask* __restrict__ tasks, const real* __restrict__ are
     }
 }
 
-// C_mapped[r, c] -= sum_i P[k+i, r] Q[k+i, c], i < f = m - rank.
+// C_mapped[r, c] -= sum_i P[k+i, r] Q[k+i, c], i < f = m - rank.  For an
+// SPD factorization (P = Q) the update is symmetric: only the tiles on or
+// below the diagonal compute, and each writes its elements to both (r, c)
+// and (c, r) -- bitwise the values the full product would give, since
+// P[., r] Q[., c] and P[., c] Q[., r] are the same products summed in the
+// same order.
 template <typename real>
 __global__ void __launch_bounds__(256)
 schur_kernel(const SchurTask* __restrict__ tasks, const real* __restrict__ fac,
@@ -200,6 +205,8 @@ schur_kernel(const SchurTask* __restrict__ tasks, const real* __restrict__ fac,
   const int N = tk.nw;
   const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
   if (i0 >= N || j0 >= N) return;
+  const bool sym = tk.P == tk.Q;
+  if (sym && j0 > i0) return;
   __shared__ real As[TK][TM + 1];
   __shared__ real Bs[TK][TN + 1];
   const real* P = fac + tk.P + k;
@@ -275,9 +282,14 @@ schur_kernel(const SchurTask* __restrict__ tasks, const real* __restrict__ fac,
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       const int jj = tx + 16 * q, gj = j0 + jj;
-      if (gj >= N) continue;
+      if (gj >= N || (sym && gj > gi)) continue;
       const int64_t addr = bs[a * tk.nb + cblk[jj]] + lr + cloc[jj] * lda;
       arena[addr] -= acc[p][q];
+      if (sym && gj != gi) {
+        // the mirror element (c, r): row gj of block (cblk, a), column gi
+        const int b = cblk[jj];
+        arena[bs[b * tk.nb + a] + cloc[jj] + (int64_t)lr * ldv[b]] -= acc[p][q];
+      }
     }
   }
 }
