@@ -207,8 +207,11 @@ schur_kernel(const SchurTask* __restrict__ tasks, const real* __restrict__ fac,
   if (i0 >= N || j0 >= N) return;
   const bool sym = tk.P == tk.Q;
   if (sym && j0 > i0) return;
-  __shared__ real As[TK][TM + 1];
-  __shared__ real Bs[TK][TN + 1];
+  // the operand tiles, then (after the products) the output tile Cs[j][i]
+  __shared__ real tile[TN * (TM + 1)];
+  real(*As)[TM + 1] = reinterpret_cast<real(*)[TM + 1]>(tile);
+  real(*Bs)[TN + 1] = reinterpret_cast<real(*)[TN + 1]>(tile + TK * (TM + 1));
+  real(*Cs)[TM + 1] = reinterpret_cast<real(*)[TM + 1]>(tile);
   const real* P = fac + tk.P + k;
   const real* Q = fac + tk.Q + k;
   const int ld = tk.m;
@@ -270,27 +273,29 @@ schur_kernel(const SchurTask* __restrict__ tasks, const real* __restrict__ fac,
       cloc[e - TM] = lr;
     }
   }
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) Cs[tx + 16 * q][ty + 16 * p] = acc[p][q];
   __syncthreads();
+  // read-modify-write of the target blocks from the staged tile, consecutive
+  // threads on consecutive rows of a block (column-major: contiguous)
   const int64_t* bs = base + tk.base;
   const int* ldv = ldn + tk.ldn;
-#pragma unroll
-  for (int p = 0; p < 4; p++) {
-    const int ii = ty + 16 * p, gi = i0 + ii;
-    if (gi >= N) continue;
-    const int a = rblk[ii], lr = rloc[ii];
-    const int64_t lda = ldv[a];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int jj = tx + 16 * q, gj = j0 + jj;
-      if (gj >= N || (sym && gj > gi)) continue;
-      const int64_t addr = bs[a * tk.nb + cblk[jj]] + lr + cloc[jj] * lda;
-      arena[addr] -= acc[p][q];
-      if (sym && gj != gi) {
-        // the mirror element (c, r): row gj of block (cblk, a), column gi
-        const int b = cblk[jj];
-        arena[bs[b * tk.nb + a] + cloc[jj] + (int64_t)lr * ldv[b]] -= acc[p][q];
-      }
-    }
+  for (int e = threadIdx.x; e < TM * TN; e += blockDim.x) {
+    const int ii = e % TM, jj = e / TM, gi = i0 + ii, gj = j0 + jj;
+    if (gi >= N || gj >= N || (sym && gj > gi)) continue;
+    const int a = rblk[ii];
+    arena[bs[a * tk.nb + cblk[jj]] + rloc[ii] + (int64_t)cloc[jj] * ldv[a]] -= Cs[jj][ii];
+  }
+  if (!sym) return;
+  // the mirror elements (c, r) of the strictly lower part: row gj of block
+  // (cblk, rblk), column gi; consecutive threads on consecutive rows gj
+  for (int e = threadIdx.x; e < TM * TN; e += blockDim.x) {
+    const int jj = e % TN, ii = e / TN, gi = i0 + ii, gj = j0 + jj;
+    if (gi >= N || gj >= gi) continue;
+    const int b = cblk[jj];
+    arena[bs[b * tk.nb + rblk[ii]] + cloc[jj] + (int64_t)rloc[ii] * ldv[b]] -= Cs[jj][ii];
   }
 }
 
