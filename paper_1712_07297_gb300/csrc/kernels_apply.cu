@@ -298,6 +298,7 @@ bwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
 // reads every slot of its cluster before any is written, so no separate z
 // pass is needed.
 constexpr int kZtMax = 256;
+constexpr int kRowsInFlight = 4;  // output rows a warp of bwd_zt works on at once
 
 template <typename real, int RB>
 __global__ void __launch_bounds__(256)
@@ -324,20 +325,37 @@ bwd_zt_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
   __syncthreads();
   const real* TRt = fac + (rc.sym ? rc.T : rc.TR);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int i = warp; i < m; i += nwarp) {
-    const real* col = TRt + (int64_t)i * m;
-    real acc[RB];
+  // kRowsInFlight output rows per warp at a time (rows i0 + w nwarp), so
+  // that their operator loads overlap; every row's sum runs in the same
+  // order as one row at a time
+  for (int i0 = warp; i0 < m; i0 += nwarp * kRowsInFlight) {
+    real acc[kRowsInFlight][RB];
 #pragma unroll
-    for (int r = 0; r < RB; r++) acc[r] = 0;
+    for (int w = 0; w < kRowsInFlight; w++)
+#pragma unroll
+      for (int r = 0; r < RB; r++) acc[w][r] = 0;
     for (int l = lane; l < m; l += 32) {
-      const real t = col[l];
+      real t[kRowsInFlight];
+#pragma unroll
+      for (int w = 0; w < kRowsInFlight; w++) {
+        const int i = i0 + w * nwarp;
+        t[w] = i < m ? TRt[(int64_t)i * m + l] : real(0);
+      }
 #pragma unroll
       for (int r = 0; r < RB; r++)
-        if (r < g.nr) acc[r] += t * zsm[r * m + l];
+        if (r < g.nr) {
+          const real zv = zsm[r * m + l];
+#pragma unroll
+          for (int w = 0; w < kRowsInFlight; w++) acc[w][r] += t[w] * zv;
+        }
     }
-    int rr;
-    const real tot = warp_sums<real, RB>(acc, &rr);
-    if (rr >= 0 && rr < g.nr) y[rc.voff + i + (int64_t)(g.r0 + rr) * ldy] = tot;
+#pragma unroll
+    for (int w = 0; w < kRowsInFlight; w++) {
+      const int i = i0 + w * nwarp;
+      int rr;
+      const real tot = warp_sums<real, RB>(acc[w], &rr);
+      if (i < m && rr >= 0 && rr < g.nr) y[rc.voff + i + (int64_t)(g.r0 + rr) * ldy] = tot;
+    }
   }
 }
 
