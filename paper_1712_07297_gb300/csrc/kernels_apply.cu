@@ -298,7 +298,10 @@ bwd_t_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
 // reads every slot of its cluster before any is written, so no separate z
 // pass is needed.
 constexpr int kZtMax = 256;
-constexpr int kRowsInFlight = 4;  // output rows a warp of bwd_zt works on at once
+// output rows a warp of bwd_zt works on at once: 8 in float32, 4 in float64
+// (8 float64 rows x 8 right-hand sides of accumulators cost occupancy)
+template <typename real>
+__host__ __device__ constexpr int rows_in_flight() { return sizeof(real) == 4 ? 8 : 4; }
 
 template <typename real, int RB>
 __global__ void __launch_bounds__(256)
@@ -325,9 +328,10 @@ bwd_zt_kernel(const ApplyRec* __restrict__ recs, const int* __restrict__ ids,
   __syncthreads();
   const real* TRt = fac + (rc.sym ? rc.T : rc.TR);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  // kRowsInFlight output rows per warp at a time (rows i0 + w nwarp), so
+  // several output rows per warp at a time (rows i0 + w nwarp), so
   // that their operator loads overlap; every row's sum runs in the same
   // order as one row at a time
+  constexpr int kRowsInFlight = rows_in_flight<real>();
   for (int i0 = warp; i0 < m; i0 += nwarp * kRowsInFlight) {
     real acc[kRowsInFlight][RB];
 #pragma unroll
