@@ -181,6 +181,30 @@ def test_lu_top_one_cluster(hs, precision):
     s.close()
 
 
+def test_top_size_above_the_dense_top_limit_is_rejected(hs):
+    # a merged dense top must fit one slot vector of the sweeps in shared
+    # memory (24,576 unknowns in float64) and, for a general matrix, the first
+    # LU panel in one 16-CTA thread-block cluster (24,816): a larger top_size
+    # is an argument error of hsolve_factor, raised before any device work
+    p = I.poisson((12, 12))
+    s = hs.Solver.from_problem(p, leaf_size=16, symmetric=1, top_size=10 ** 6)
+    with pytest.raises(hs.HsolveError) as e:
+        s.factor(1e-2, "fp64")
+    assert e.value.code == -1
+    s.close()
+    s = hs.Solver.from_problem(p, leaf_size=16, symmetric=1, top_size=24576)
+    s.factor(1e-2, "fp64")  # at the limit: the whole 144-unknown matrix is the top
+    assert s.stats()["top_size"] == p.n
+    s.close()
+    q = I.convection_diffusion((12, 12))
+    s = hs.Solver.from_problem(q, leaf_size=16, symmetric=0, top_size=30000)
+    for prec in ("fp64", "mixed_fp32"):
+        with pytest.raises(hs.HsolveError) as e:
+            s.factor(1e-2, prec)
+        assert e.value.code == -1
+    s.close()
+
+
 @pytest.mark.parametrize("name,mk,leaf,eps", [
     ("poisson2d_64", lambda: I.poisson((64, 64)), 64, 1e-3),
     ("poisson3d_16", lambda: I.poisson((16, 16, 16)), 64, 1e-2),
