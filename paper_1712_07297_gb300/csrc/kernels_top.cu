@@ -1,26 +1,32 @@
-// Dense top factorization (Alg. 1: "factorize A with the conventional
-// Cholesky factorization" once the remaining system is small enough), for an
-// SPD top block too large for one CTA: blocked right-looking Cholesky over
-// 64-column panels (one CTA factors the diagonal block, a launch of CTAs
-// solves the panel, a launch updates the trailing lower triangle), then the
-// explicit inverse factor X = L^{-1} by block rows (one launch per block
-// row, one CTA per block column), which the substitution sweeps apply as
-// dense products.  Matrices are column-major in global memory.
+// Dense top factorization (Alg. 1: the remaining system is factored with a
+// conventional dense factorization once it is small enough).
 //
-// A general (nonsymmetric) top goes through a blocked right-looking LU with
-// partial pivoting instead.  Each panel of nb columns (128 bytes of a row:
-// 32 float32 or 16 float64 columns) is factored by one thread-block cluster
-// that holds the whole tall panel in distributed shared memory: per column
-// the CTAs agree on the pivot through two cluster barriers (largest |a| over
-// the remaining rows, then the lowest current row among the entries within
-// 1e-10 of it, the tie rule of the one-CTA LU), and row interchanges inside
-// the panel are relabellings, not copies.  Then one launch applies the
-// panel's interchanges to the other columns, one solves the unit-lower
-// system for the block row of U, and the trailing update is a tensor-core
-// 3xTF32 product (float32) or a SIMT product (float64).  The stored
-// operators follow from A = P^T L U: T' = L^{-1} P (the inverse of the unit
-// lower factor, columns scattered by the row order) and T'_R^T = U^{-T},
-// both by block rows as for the Cholesky top.
+// SPD top too large for one CTA (float64; the float32 modes use the
+// tensor-core recursion of the tcgen05 kernels): blocked right-looking
+// Cholesky over 64-column panels (one CTA factors the diagonal block, a
+// launch of CTAs solves the panel, a launch updates the trailing lower
+// triangle), then the explicit inverse factor X = L^{-1} recursively: the
+// 64 x 64 diagonal blocks inverted in one launch, then X21 = -X22 (L21 X11)
+// per split, as matrix products.  The substitution sweeps apply X as dense
+// products.  Matrices are column-major in global memory.
+//
+// General (nonsymmetric) top (Sec. 6): recursive LU with partial pivoting
+// over column halves -- left half, U12 = X11 A12, A22 -= L21 U12, right half
+// -- that grows the inverse factors X = L^{-1} and Z = U^{-T} with it
+// (X21 = -X22 (L21 X11), Z21 = -Z22 (U12^T Z11)).  A leaf is one panel of nb
+// columns (128 bytes of a row: 32 float32 or 16 float64 columns) factored by
+// one thread-block cluster that holds the whole tall panel in distributed
+// shared memory: per column one cluster barrier, after which every CTA reads
+// each CTA's largest |a| over the remaining rows and its lowest current row
+// within 1e-10 of that, and takes the lowest such row within 1e-10 of the
+// overall maximum (the tie rule of the one-CTA LU, applied per CTA); row
+// interchanges inside the panel are relabellings, not copies, and the
+// panel's diagonal blocks of X and Z come out with it; a second launch
+// applies the panel's interchanges to every other column.  The products run
+// on the tensor cores (3xTF32) in float32 and on the SIMT units in float64
+// (skipping the zero chunks of triangular operands).  The stored operators
+// follow from A = P^T L U: T' = L^{-1} P (the columns of X scattered by the
+// row order) and T'_R^T = Z.
 #include <algorithm>
 #include <climits>
 #include <type_traits>
