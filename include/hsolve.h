@@ -160,9 +160,14 @@ hsolve_status hsolve_analyze(const hsolve_csr* A, const double* coords, int dim,
  * perm).  eps is the relative compression tolerance of Eq. lra (|r_jj| <=
  * eps |r_11| stops the pivoted QR; 0 keeps every nonzero direction, i.e. a
  * direct solver).  May be called again on the same analysis with another eps
- * or precision; the previous factorization is released first.  Errors:
- * HSOLVE_ERR_NOT_SPD / HSOLVE_ERR_SINGULAR (cluster pivot failure; the handle
- * then holds no factorization), HSOLVE_ERR_OOM, HSOLVE_ERR_CUDA. */
+ * or precision; the previous factorization is released first.  Once a level
+ * holds at most opts.top_size unknowns (or one cluster is left) it is
+ * factored densely: Cholesky for an SPD matrix, LU with partial pivoting
+ * otherwise (Alg. 1's "small enough", Sec. 6).  Errors: HSOLVE_ERR_ARG for a
+ * bad eps or precision, or a top_size above the dense-top limit (see
+ * hsolve_opts.top_size); HSOLVE_ERR_NOT_SPD / HSOLVE_ERR_SINGULAR (pivot
+ * failure in a cluster or the dense top; the handle then holds no
+ * factorization), HSOLVE_ERR_OOM, HSOLVE_ERR_CUDA. */
 hsolve_status hsolve_factor(hsolve_handle* h, double eps, hsolve_precision prec);
 
 /* Test entry point: hsolve_factor with the rank of every cluster fixed in
